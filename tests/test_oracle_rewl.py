@@ -1,0 +1,379 @@
+"""Pins of the REWL oracle (oracle/rewl_oracle.c) against what the paper and
+the mathematics fix, independently of the oracle's own code.
+
+Sec. 2: windows with ~75% overlap, m independent WL walkers each, acceptance
+min[1, g(E_old)/g(E_new)], ln g(E) += ln f and H(E) += 1 every step, flatness
+of every walker, averaging of ln g within a window, f -> sqrt f, replica
+exchange with Eq. 1, joining at the best-matching slope (Fig. 2).
+Sec. 3.1: 717 windows with 75% overlap for L=300 (pins the window formula).
+"""
+import math
+import subprocess
+import sys
+import textwrap
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+
+
+# --------------------------------------------------------------------------
+# Philox4x32-10
+def test_philox_matches_independent_implementation():
+    """Triton ships its own Philox4x32-10 (run here in its CPU interpreter);
+    both follow Salmon et al. (SC'11) and must agree word for word."""
+    pytest.importorskip("triton")
+    script = textwrap.dedent(
+        """
+        import os, json
+        os.environ["TRITON_INTERPRET"] = "1"
+        import torch, triton, triton.language as tl
+        @triton.jit
+        def k(out, c0p, c1p, c2p, c3p, seed):
+            i = tl.arange(0, 8)
+            a, b, c, d = tl.philox(seed, tl.load(c0p + i), tl.load(c1p + i), tl.load(c2p + i), tl.load(c3p + i))
+            tl.store(out + i * 4 + 0, a); tl.store(out + i * 4 + 1, b)
+            tl.store(out + i * 4 + 2, c); tl.store(out + i * 4 + 3, d)
+        ctr = [[0, 0, 0, 0], [1, 2, 3, 4], [0xffffffff] * 4, [12345, 777, 5, 2],
+               [7, 0, 1023, 0], [0x80000000, 1, 0, 3], [999, 999, 999, 999], [42, 0, 0, 4]]
+        res = {}
+        for seed in (0, 1, 0x5EED0003, 0x123456789abcdef):
+            cols = [torch.tensor([c[j] for c in ctr], dtype=torch.uint32) for j in range(4)]
+            out = torch.zeros(32, dtype=torch.uint32)
+            k[(1,)](out, *cols, seed)
+            res[str(seed)] = out.view(8, 4).tolist()
+        print(json.dumps({"ctr": ctr, "res": res}))
+        """
+    )
+    p = subprocess.run([sys.executable, "-c", script], capture_output=True, text=True, timeout=600)
+    if p.returncode != 0:
+        pytest.skip("triton interpreter unavailable: " + p.stderr[-200:])
+    import json
+    data = json.loads(p.stdout.strip().splitlines()[-1])
+    for seed_s, rows in data["res"].items():
+        seed = int(seed_s)
+        key = [seed & 0xFFFFFFFF, seed >> 32]
+        for ctr, want in zip(data["ctr"], rows):
+            got = O.philox4x32_10(ctr, key)
+            assert [int(x) for x in got] == [int(x) & 0xFFFFFFFF for x in want]
+
+
+# --------------------------------------------------------------------------
+# Windows
+def test_window_formula_reproduces_paper_geometry():
+    """Sec. 3.1: L=300 split into 717 windows with 75% overlap."""
+    e_lo, W = O.window_table(300, 717, 0.75)
+    N = 300 * 300
+    assert W == 1000
+    assert e_lo[0] == -2 * N and e_lo[-1] + W == 0
+    assert set(np.diff(e_lo).tolist()) == {250}
+    assert 1 - 250 / W == 0.75
+
+
+def test_window_tables_of_the_workloads():
+    e_lo, W = O.window_table(8, 4, 0.75)
+    assert W == 74 and e_lo.tolist() == [-128, -110, -92, -74]
+    e_lo, W = O.window_table(20, 8, 0.75)
+    assert W == 291 and (e_lo + 800).tolist() == [0, 73, 145, 218, 291, 364, 436, 509]
+    _, W = O.window_table(80, 64, 0.75)
+    assert W == 765
+
+
+@pytest.mark.parametrize("L,h,o", [(5, 2, 0.5), (12, 3, 0.75), (16, 7, 0.6), (33, 16, 0.75), (48, 4, 0.75), (96, 64, 0.8)])
+def test_window_invariants(L, h, o):
+    N = L * L
+    e_lo, W = O.window_table(L, h, o)
+    assert e_lo[0] == -2 * N and e_lo[-1] + W == 0
+    if h > 1:
+        d = np.diff(e_lo)
+        assert d.max() - d.min() <= 1 and d.min() > 0
+        assert (W - d.max()) >= o * W - 1.0  # overlap of neighbours is at least ~o
+
+
+# --------------------------------------------------------------------------
+# Merge arithmetic (pairwise tree in index order, then / m)
+def test_tree_mean_hand_cases():
+    e = 2.0 ** -53
+    # m=3: ((a + b) + c) / 3.  (1 + e) rounds to 1, so the sum is 1; the other
+    # association 1 + (e + e) would give 1 + 2^-52.
+    assert O.tree_mean([1.0, e, e]) == 1.0 / 3.0
+    # m=4: ((a + b) + (c + d)) / 4: (1 + e) -> 1, (e + e) = 2^-52, 1 + 2^-52 exact.
+    assert O.tree_mean([1.0, e, e, e]) == (1.0 + 2.0 ** -52) / 4.0
+    # m=5: (((a+b)+(c+d)) + e5) / 5
+    assert O.tree_mean([3.0, 5.0, 7.0, 9.0, 11.0]) == 7.0
+    assert O.tree_mean([0.1]) == 0.1
+    assert O.tree_mean([0.3] * 16) == 0.3
+
+
+# --------------------------------------------------------------------------
+# Single WL steps
+def _fresh(q=2, L=4, h=1, o=0.75, m=1, lnf_final=1e-6, flat=0.8, K=1000, seed=7):
+    return O.OracleREWL(q, L, h, o, m, lnf_final, flat, K, seed)
+
+
+def test_walkers_start_inside_their_windows_and_energy_is_consistent():
+    r = O.OracleREWL(10, 12, 6, 0.75, 3, 1e-6, 0.8, 2000, 11)
+    E, e_lo, sig = r.E(), r.e_lo(), r.sigma()
+    for g in range(r.G):
+        w = g // r.m
+        assert e_lo[w] <= E[g] <= e_lo[w] + r.W
+        assert O.energy(r.L, sig[g]) == E[g]
+    for _ in range(5):
+        r.sweep()
+        r.barrier()
+    E, sig = r.E(), r.sigma()
+    for g in range(r.G):
+        w = g // r.m
+        assert O.energy(r.L, sig[g]) == E[g]
+        assert e_lo[w] <= E[g] <= e_lo[w] + r.W
+    assert np.all(sig < 10)
+
+
+def test_every_step_adds_lnf_and_one_visit():
+    r = _fresh(q=3, L=5, h=2, m=2, K=777)
+    lnf = r.lnf().copy()
+    r.sweep()
+    H, lng, t = r.H(), r.lng(), r.t()
+    assert np.all(H.sum(axis=1) == 777)
+    assert np.all(t == 777)
+    # ln g grows by exactly ln f per visit (ln f = 1: the sums are exact integers)
+    assert np.array_equal(lng, H.astype(np.float64) * lnf[0])
+
+
+@pytest.mark.parametrize("q,L,h", [(2, 4, 1), (3, 3, 1), (2, 4, 2)])
+def test_fixed_weights_give_a_flat_histogram(q, L, h):
+    """With ln g = the exact ln g and ln f = 0, acceptance min[1, g(E)/g(E')]
+    samples configurations with weight 1/g(E): every reachable energy of the
+    window is visited equally often (multicanonical identity).  A wrong sign,
+    a dropped term or a biased proposal breaks the flatness by far more than
+    the statistical tolerance."""
+    N = L * L
+    ex = O.exact_lng(O.exact_counts_brute(q, L))
+    r = _fresh(q=q, L=L, h=h, m=1, seed=3)
+    e_lo = r.e_lo()
+    tab = np.zeros((r.G, r.B))
+    for w in range(h):
+        seg = ex[e_lo[w] + 2 * N: e_lo[w] + 2 * N + r.B]
+        tab[w] = np.where(np.isfinite(seg), seg, 0.0)
+    r.set_lng(tab)
+    r.set_lnf(0.0)
+    for g in range(r.G):
+        r.wl_steps(g, 4_000_000)
+    H = r.H()
+    for w in range(h):
+        seg = ex[e_lo[w] + 2 * N: e_lo[w] + 2 * N + r.B]
+        reach = np.isfinite(seg)
+        assert np.all(H[w][~reach] == 0)
+        hv = H[w][reach].astype(float)
+        assert np.max(np.abs(hv / hv.mean() - 1)) < 0.03
+
+
+def test_out_of_window_proposals_are_rejected_but_counted():
+    r = _fresh(q=2, L=6, h=4, m=1, K=5000, seed=9)
+    e_lo = r.e_lo()
+    r.sweep()
+    H, E = r.H(), r.E()
+    for g in range(r.G):
+        assert H[g].sum() == 5000
+        assert e_lo[g] <= E[g] <= e_lo[g] + r.W
+
+
+# --------------------------------------------------------------------------
+# Flatness, merge, f-reduction
+def test_flatness_merge_and_f_reduction():
+    r = _fresh(q=2, L=4, h=1, m=3, lnf_final=0.3, seed=1)
+    B = r.B
+    mask = np.zeros((1, B), np.uint8)
+    mask[0, [2, 4, 6]] = 1
+    r.set_mask(mask)
+    H = np.zeros((3, B), np.uint32)
+    H[:, [2, 4, 6]] = [[10, 10, 10], [9, 10, 11], [10, 10, 10]]
+    H[1, 8] = 1000  # outside the mask: ignored by the flatness test
+    r.set_H(H)
+    assert r.walker_flat(0) and r.walker_flat(1) and r.walker_flat(2)
+    lng = np.zeros((3, B))
+    lng[:, 2] = [1.0, 2.0, 4.0]
+    lng[:, 4] = [0.5, 0.5, 0.5]
+    r.set_lng(lng)
+    r.window_iterations()
+    out = r.lng()
+    assert np.all(out[:, 2] == (3.0 + 4.0) / 3.0)
+    assert np.all(out[:, 4] == 0.5)
+    assert np.all(r.H() == 0)
+    assert r.lnf()[0] == 0.5 and r.iter()[0] == 1 and not r.done()[0]
+    # a walker with min < 0.8 * mean blocks the whole window
+    H[:, [2, 4, 6]] = [[10, 10, 10], [7, 10, 13], [10, 10, 10]]
+    r.set_H(H)
+    assert not r.walker_flat(1)
+    before = r.lng().copy()
+    r.window_iterations()
+    assert r.lnf()[0] == 0.5 and np.array_equal(r.lng(), before)
+    # next flat iteration: ln f 0.5 -> 0.25 < 0.3: finished
+    H[:, [2, 4, 6]] = 10
+    r.set_H(H)
+    r.window_iterations()
+    assert r.lnf()[0] == 0.25 and r.done()[0] == 1
+
+
+def test_iteration_count_of_the_halving_schedule():
+    """ln f = 1, 1/2, ...: stop once ln f < ln f_final.  1e-6 -> 20 halvings."""
+    r = O.OracleREWL(2, 4, 1, 0.75, 1, 1e-6, 0.8, 2000, 5)
+    assert r.run(0)
+    assert r.iter()[0] == 20 and r.lnf()[0] == 2.0 ** -20
+
+
+# --------------------------------------------------------------------------
+# Replica exchange (Eq. 1)
+def _exchange_fixture(seed=4):
+    q, L = 2, 4
+    r = O.OracleREWL(q, L, 2, 0.75, 1, 1e-6, 0.8, 1000, seed)
+    return r
+
+
+def test_exchange_acceptance_follows_eq1():
+    """Two walkers in neighbouring windows with energies in the overlap: the
+    swap is accepted with min[1, g_i(E_X) g_j(E_Y) / (g_i(E_Y) g_j(E_X))]."""
+    r = _exchange_fixture()
+    N, B = r.N, r.B
+    e_lo = r.e_lo()
+    lo = max(e_lo[1], e_lo[0])
+    hi = min(e_lo[0], e_lo[1]) + r.W
+    # two configurations with distinct energies inside the overlap
+    rng = np.random.default_rng(0)
+    cfgs = {}
+    while len(cfgs) < 2:
+        s = rng.integers(0, 2, N).astype(np.uint8)
+        e = O.energy(r.L, s)
+        if lo <= e <= hi:
+            cfgs.setdefault(e, s)
+    (Ex, X), (Ey, Y) = sorted(cfgs.items())
+    for target in (0.3, 0.75, 1.0):
+        lng = np.zeros((2, B))
+        # ln g_i(E_X) - ln g_i(E_Y) + ln g_j(E_Y) - ln g_j(E_X) = ln(target)
+        lng[0, Ex - e_lo[0]] = math.log(target) / 2
+        lng[1, Ey - e_lo[1]] = math.log(target) / 2
+        r.set_lng(lng)
+        acc, trials = 0, 4000
+        for t in range(trials):
+            r.set_config(0, X)
+            r.set_config(1, Y)
+            r.set_round(2 * t)  # even rounds pair window 0 with window 1
+            r.exchange()
+            acc += int(r.E()[0] == Ey)
+        p = acc / trials
+        if target == 1.0:
+            assert acc == trials
+        else:
+            assert abs(p - target) < 4 * math.sqrt(target * (1 - target) / trials)
+    # odd rounds have no pair with h = 2
+    r.set_config(0, X)
+    r.set_config(1, Y)
+    r.set_round(1)
+    r.exchange()
+    assert r.E()[0] == Ex
+
+
+def test_exchange_swaps_configuration_energy_and_replica_id_together():
+    r = O.OracleREWL(3, 6, 4, 0.75, 4, 1e-6, 0.8, 3000, 21)
+    for _ in range(30):
+        r.sweep()
+        r.barrier()
+    rep, E, sig = r.rep(), r.E(), r.sigma()
+    assert sorted(rep.tolist()) == list(range(r.G))
+    for g in range(r.G):
+        assert O.energy(r.L, sig[g]) == E[g]
+    assert r.xstats()[1] > 0  # some swaps happened
+
+
+# --------------------------------------------------------------------------
+# Joining and normalisation (Sec. 2, Fig. 2)
+@pytest.mark.parametrize("q,L,h", [(2, 8, 4), (10, 4, 3), (3, 4, 5)])
+def test_join_recovers_exact_pieces(q, L, h):
+    """Cut the exact ln g into the windows, shift every piece by a random
+    constant, join and normalise: the exact ln g comes back."""
+    N = L * L
+    ex = O.exact_lng(O.exact_counts_tm(q, L))
+    e_lo, W = O.window_table(L, h, 0.75)
+    B = W + 1
+    rng = np.random.default_rng(1)
+    lw = np.zeros((h, B))
+    mw = np.zeros((h, B), np.uint8)
+    for w in range(h):
+        seg = ex[e_lo[w] + 2 * N: e_lo[w] + 2 * N + B]
+        mw[w] = np.isfinite(seg)
+        lw[w] = np.where(mw[w] > 0, seg + rng.normal() * 50, 0.0)
+    out = O.normalise(q, N, O.join_pieces(N, e_lo, W, lw, mw))
+    fin = np.isfinite(ex)
+    assert np.array_equal(np.isfinite(out), fin)
+    assert np.max(np.abs(out[fin] - ex[fin])) < 1e-9
+
+
+def test_normalise_gives_q_to_the_N_total():
+    q, N = 10, 16
+    v = np.full(2 * N + 1, -np.inf)
+    v[[0, 4, 8, 20]] = [0.0, 3.0, 1.0, 30.0]
+    out = O.normalise(q, N, v)
+    fin = np.isfinite(out)
+    total = np.log(np.sum(np.exp(out[fin] - out[fin].max()))) + out[fin].max()
+    assert abs(total - N * math.log(q)) < 1e-12
+    assert np.allclose(np.diff(out[[0, 4, 8, 20]]), np.diff(v[[0, 4, 8, 20]]))
+
+
+# --------------------------------------------------------------------------
+# Whole runs against exact densities of states
+def _run_error(q, L, h, m, lnf_final, K, seed):
+    N = L * L
+    ex = O.exact_lng(O.exact_counts_tm(q, L))
+    r = O.OracleREWL(q, L, h, 0.75, m, lnf_final, 0.8, K, seed)
+    assert r.run(0)
+    lg = r.lng_joined()
+    fin = np.isfinite(ex)
+    # the visited bins are exactly the reachable ones
+    assert np.array_equal(np.isfinite(lg), fin)
+    return lg, ex, fin
+
+
+@pytest.mark.parametrize("q,L,h,m", [(2, 4, 2, 2), (3, 3, 2, 2), (10, 4, 3, 2)])
+def test_small_runs_are_close_to_exact(q, L, h, m):
+    errs = []
+    for seed in (1, 2, 3):
+        lg, ex, fin = _run_error(q, L, h, m, 1e-6, 2000, seed)
+        errs.append(np.max(np.abs(lg[fin] - ex[fin])))
+        assert abs(lg[0] - math.log(q)) < 0.2  # g(ground) = q
+    assert np.median(errs) < 0.15
+
+
+def test_ising_L8_sixteen_seed_mean_within_005():
+    """q=2, L=8, h=4, m=2, ln f_final = 1e-6, flatness 0.8, 10^4 steps between
+    exchanges, seeds 1..16: the mean of the 16 normalised ln g lies within 0.05
+    of the exact ln g in every bin; single runs stay within 0.35 (their spread
+    is statistical: it shrinks as 1/sqrt(m), Sec. 2)."""
+    runs = []
+    for seed in range(1, 17):
+        lg, ex, fin = _run_error(2, 8, 4, 2, 1e-6, 10000, seed)
+        assert np.max(np.abs(lg[fin] - ex[fin])) < 0.35
+        runs.append(lg[fin])
+    mean = np.full(129, -np.inf)
+    mean[fin] = np.mean(runs, axis=0)
+    mean = O.normalise(2, 64, mean)
+    assert np.max(np.abs(mean[fin] - ex[fin])) < 0.05
+
+
+def test_error_shrinks_with_more_walkers():
+    """Sec. 2: averaging over m walkers lowers the statistical error ~ 1/sqrt(m)."""
+    def med(m):
+        return np.median([np.max(np.abs(a[f] - e[f])) for a, e, f in
+                          (_run_error(2, 4, 1, m, 1e-5, 2000, s) for s in range(1, 13))])
+    e1, e8 = med(1), med(8)
+    assert e8 < e1 / 1.8
+
+
+def test_runs_are_deterministic_in_the_seed():
+    a = O.OracleREWL(3, 5, 3, 0.75, 2, 1e-3, 0.8, 1000, 99)
+    b = O.OracleREWL(3, 5, 3, 0.75, 2, 1e-3, 0.8, 1000, 99)
+    c = O.OracleREWL(3, 5, 3, 0.75, 2, 1e-3, 0.8, 1000, 100)
+    for r in (a, b, c):
+        r.run(20)
+    assert np.array_equal(a.lng(), b.lng()) and np.array_equal(a.sigma(), b.sigma())
+    assert not np.array_equal(a.lng(), c.lng())
