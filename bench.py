@@ -1,0 +1,313 @@
+#!/usr/bin/env python3
+"""Benchmark of the REWL hot path (arXiv:1312.3004, Sec. 2) on one GB300.
+
+Workload (default): 10-state Potts model, L = 80 (N = 6400) on a torus,
+h = 64 windows with 75% overlap, m = 16 walkers per window (1024 walkers),
+4-bit packed spins, FP64 ln g, 10^4 WL steps per walker between exchanges,
+ln f_final = 1e-8, flatness 0.8; synthetic (seeded) initial states.
+
+One step = one exchange round: K WL proposals for every walker of every
+unfinished window (sweep kernel), then flatness / merge / f-reduction (check
+kernel) and the replica exchange (exchange kernel).  Reported value: WL flip
+attempts per second over the timed steps (device events on the launching
+stream), L2 flushed between steps.  Prints one JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 (torchrun) every rank runs an independent replica (seed + rank):
+there is no data exchange between instances, so scaling is weak.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+# Algorithmic lane-operations of one WL proposal (integer / logic / shared-memory
+# slots that the method needs per flip; FP64 counted separately):
+#   Philox4x32-10 10 x (2 wide multiplies + 2 three-input XORs) + counter = 42
+#   site, new value, x/y split and 4 wrapped neighbour indices           = 14
+#   5 spin reads + 4-bit extraction                                      = 15
+#   dE (8 compares + 7 adds)                                             = 15
+#   window test 2, ln g reads 2, accept compare 1, u construction 4      =  9
+#   conditional spin write 3, ln g store 2, H read-add-store 3           =  8
+ALG_OPS_PER_FLIP = 103
+ALG_FP64_PER_FLIP = 2  # D = ln g(E) - ln g(E'), ln g(E) += ln f
+SMS = 152
+LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="potts10_L80")
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi samples every 200 ms during the timed region."""
+
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 10:
+                continue
+            if self.uuid and parts[1] != self.uuid:
+                continue
+            rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+def cpu_baseline(p, seed, budget_s):
+    """The oracle, as it stands, on this host: rounds of the same workload until
+    about budget_s seconds of CPU work (at least one round)."""
+    from oracle import oracle as O
+    from paper_1312_3004_gb300 import workloads as WL
+
+    t0 = time.perf_counter()
+    orc = O.OracleREWL(*WL.rewl_args(p, seed))
+    t_create = time.perf_counter() - t0
+    rounds, t_run = 0, 0.0
+    walkers = p["h"] * p["m"]
+    while t_run < budget_s and rounds < 1000:
+        t0 = time.perf_counter()
+        orc.run(1)
+        t_run += time.perf_counter() - t0
+        rounds += 1
+    flips = rounds * walkers * p["exchange_interval"]
+    return {"value": flips / t_run, "unit": "flips/s", "cores": 1, "kind": "oracle",
+            "sample": "%d exchange round(s) of the %d-walker workload (%d WL proposals, %.1f s), "
+                      "after a %.1f s set-up; single-threaded C" % (rounds, walkers, flips, t_run, t_create)}
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle timed on the host cores."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_1312_3004_gb300 import workloads as WL
+
+    p = WL.params(args.workload)
+    orc = O.OracleREWL(*WL.rewl_args(p, args.seed))
+    walkers = p["h"] * p["m"]
+    for _ in range(args.warmup):
+        orc.run(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        orc.run(1)
+    dt = time.perf_counter() - t0
+    flips = args.steps * walkers * p["exchange_interval"]
+    value = flips / dt
+    line = {
+        "impl": "reference", "metric": "flip attempts/s", "value": value, "unit": "flips/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_of(args.workload, p),
+        "cpu_baseline": {"value": value, "unit": "flips/s", "cores": 1, "kind": "oracle",
+                         "sample": "%d exchange rounds of the %d-walker workload after %d warm-up rounds"
+                                   % (args.steps, walkers, args.warmup)},
+        "e2e": {"value": value, "unit": "flips/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_of(name, p):
+    return {"workload": name, "q": p["q"], "L": p["L"], "h": p["h"], "overlap": p["overlap"],
+            "m": p["m"], "walkers": p["h"] * p["m"], "exchange_interval": p["exchange_interval"],
+            "lnf_final": p["lnf_final"], "flatness": p["flatness"], "spin_bits": p["spin_bits"],
+            "l2": "flushed between steps (256 MiB write)"}
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    from paper_1312_3004_gb300 import REWL, _lib
+    from paper_1312_3004_gb300 import workloads as WL
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    p = WL.params(args.workload)
+    stream = torch.cuda.Stream()
+    r = REWL(*WL.rewl_args(p, args.seed + rank), spin_bits=p["spin_bits"], stream=stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def one_step(ev):
+        e0, e1, e2 = ev
+        e0.record(stream)
+        r.run_phase(_lib.PHASE_SWEEP)
+        e1.record(stream)
+        r.run_phase(_lib.PHASE_CHECK)
+        r.run_phase(_lib.PHASE_EXCHANGE)
+        e2.record(stream)
+
+    for _ in range(args.warmup):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        r.run_async(1)
+    r.sync()
+
+    props = torch.cuda.get_device_properties(local)
+    uuid = getattr(props, "uuid", None)
+    uuid = ("GPU-" + str(uuid)) if uuid is not None and not str(uuid).startswith("GPU-") else uuid
+    sampler = ClockSampler(uuid if uuid else None)
+    events = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(args.steps)]
+    s0 = r.stats()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()  # L2 flush, ordered before the step, outside its events
+        one_step(events[i])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+    s1 = r.stats()
+    step_ms = [a.elapsed_time(c) for a, _, c in events]
+    sweep_ms = [a.elapsed_time(b) for a, b, _ in events]
+    total_ms = sum(step_ms)
+    flips = s1["flips"] - s0["flips"]
+
+    tot = torch.tensor([total_ms, float(flips)], dtype=torch.float64, device="cuda")
+    if dist:
+        mx = tot[:1].clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = tot[1:].clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        total_ms_max, flips_all = float(mx.item()), float(sm.item())
+    else:
+        total_ms_max, flips_all = total_ms, float(flips)
+    value = flips_all / (total_ms_max / 1e3)
+
+    # end to end through the public call: rewl_run(1 round) reads the device
+    # status block back into host memory every step
+    e2e_steps = max(3, min(args.steps, 10))
+    e0s = r.stats()["flips"]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        r.run(1)
+    e2e_s = time.perf_counter() - t0
+    e2e_flips = r.stats()["flips"] - e0s
+    e2e_local = e2e_flips / e2e_s
+    if dist:
+        t = torch.tensor([e2e_local], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        e2e_val = float(t.item())
+    else:
+        e2e_val = e2e_local
+
+    # roofline of the dominant kernel (sweep): algorithmic lane-ops per launch
+    active_walkers = flips / max(1, args.steps) / p["exchange_interval"]
+    sweep_avg_s = statistics.mean(sweep_ms) / 1e3
+    ops_per_launch = active_walkers * p["exchange_interval"] * ALG_OPS_PER_FLIP
+    achieved = ops_per_launch / sweep_avg_s / 1e12
+    peak = SMS * LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": "flip attempts/s", "value": value, "unit": "flips/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": dict(config_of(args.workload, p), parallelism="replicas" if world > 1 else "single"),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "sweep_kernel", "avg_launch_ms": sweep_avg_s * 1e3,
+                     "ops_per_flip": ALG_OPS_PER_FLIP,
+                     "peak_basis": "152 SMs x 128 INT32/FP32 lanes x 2070 MHz (recipe unit counts)"},
+        "e2e": {"value": e2e_val, "unit": "flips/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 64,
+                "call": "rewl_run(handle, 1 round) incl. status read-back", "steps": e2e_steps},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clocks,
+        "wall_s_timed": wall,
+        "sweep_share": sum(sweep_ms) / total_ms,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(p, args.seed, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

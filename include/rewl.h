@@ -1,0 +1,213 @@
+/*
+ * rewl.h -- C ABI of the GB300 (sm_103a) implementation of Replica-Exchange
+ * Wang-Landau sampling (REWL) for the periodic 2D q-state Potts model.
+ *
+ * Method: Vogel, Li, Wuest & Landau, "Exploring new frontiers in statistical
+ * physics with a new, parallel Wang-Landau framework", arXiv:1312.3004.
+ *   Sec. 2   -- the REWL scheme: the energy range is split into h windows with
+ *               overlap o; every window is sampled by m independent WL walkers
+ *               with their own ln g(E) and H(E); walkers accept single moves
+ *               with min[1, g(E_old)/g(E_new)] and add ln f to ln g(E) and 1 to
+ *               H(E) every step; once all m walkers of a window are flat their
+ *               ln g are averaged and shared, H is cleared and f -> sqrt(f);
+ *               configurations are exchanged between walkers of neighbouring
+ *               windows with the probability of Eq. 1; the run ends when every
+ *               window has reached f_final and the pieces are joined where
+ *               their slopes d ln g / dE agree best (Fig. 2).
+ *   Eq. 2    -- Potts energy E = -sum over nearest-neighbour pairs of
+ *               delta(s_i, s_j); N = L x L spins, periodic here.
+ *
+ * Conventions for every function below:
+ *   - Every call returns a rewl_status; nothing throws across the ABI.  On an
+ *     error, rewl_last_error() returns a message (thread-local, valid until the
+ *     next call on the same thread).
+ *   - A rewl_t handle owns all device memory of one REWL instance.  It lives on
+ *     the CUDA device that was current when it was created.
+ *   - Output buffers are owned by the caller.  "host" buffers must be host
+ *     memory (pageable or pinned); no function keeps a pointer to them.
+ *   - Calls on one handle are not thread-safe; distinct handles are
+ *     independent.  Work is queued on the handle's stream (see
+ *     rewl_set_stream); functions that return results to host memory
+ *     synchronise that stream.
+ *   - Energies use E in [-2N, 0]; bin index b = E + 2N in [0, 2N] is the number
+ *     of unsatisfied bonds.  Window i covers E_lo(i) .. E_lo(i) + W (W + 1 bins)
+ *     with W = ceil(2N / (1 + (h - 1)(1 - o))) and
+ *     E_lo(i) = -2N + round_half_up(i (2N - W) / (h - 1)).
+ */
+#ifndef REWL_H
+#define REWL_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rewl_s *rewl_t;
+
+typedef enum {
+    REWL_OK = 0,
+    REWL_ERR_ARG = 1,       /* an argument is out of range or a pointer is NULL   */
+    REWL_ERR_NOMEM = 2,     /* a device or host allocation failed                 */
+    REWL_ERR_CUDA = 3,      /* a CUDA runtime call failed                          */
+    REWL_ERR_TIMEOUT = 4,   /* a bounded device wait gave up                       */
+    REWL_ERR_OVERFLOW = 5,  /* a histogram bin reached 2^31 visits                 */
+    REWL_ERR_STATE = 6,     /* call not valid in the current state (see function) */
+    REWL_ERR_CANCELLED = 7  /* the job was cancelled                               */
+} rewl_status;
+
+/* Parameters of one REWL instance (Sec. 2 symbols). */
+typedef struct rewl_params {
+    int q;                        /* Potts states, 2 <= q <= 255 (<= 16 for 4-bit spins) */
+    int L;                        /* linear size, 3 <= L <= 1024; N = L * L               */
+    int h;                        /* number of energy windows, >= 1                        */
+    double overlap;               /* o, 0 <= o < 1 (0.75 in the paper)                     */
+    int m;                        /* walkers per window, 1 <= m <= 256                     */
+    double lnf_final;             /* stop once ln f < lnf_final, 0 < lnf_final < 1         */
+    double flatness;              /* p: flat iff min H >= p * mean H, 0 < p < 1            */
+    long long exchange_interval;  /* K: WL steps per walker between exchanges, >= 1       */
+    unsigned long long seed;      /* Philox4x32-10 key                                     */
+} rewl_params;
+
+/* Derived sizes of an instance, filled by rewl_get_info. */
+typedef struct rewl_info {
+    int N;              /* spins per configuration                          */
+    int W;              /* window width in energy units (W + 1 bins)         */
+    int walkers;        /* h * m                                             */
+    int spin_bits;      /* 4 or 8 bits per stored spin                       */
+    size_t device_bytes;/* device memory owned by the handle                 */
+} rewl_info;
+
+/* Per-instance counters, filled by rewl_get_stats. */
+typedef struct rewl_stats {
+    long long rounds;          /* exchange rounds completed (barriers)         */
+    long long flips;           /* WL proposals made by all walkers             */
+    long long accepted;        /* accepted WL proposals                        */
+    long long exch_tried;      /* exchange pairs evaluated with Eq. 1          */
+    long long exch_accepted;   /* exchanges carried out                        */
+    long long near_ties;       /* acceptance draws with |u - exp(D)| < 1e-14   */
+    int windows_done;          /* windows that reached ln f_final              */
+    int converged;             /* 1 when every window is done                  */
+    double min_lnf;            /* smallest ln f over windows                   */
+    double max_lnf;            /* largest ln f over windows                    */
+} rewl_stats;
+
+/* Create an instance: computes the window table, allocates the device state,
+ * draws every walker's initial configuration from the seed and moves it into
+ * its window (Sec. 3.2: each walker starts with a configuration whose energy is
+ * inside its window).  ln g = 0, H = 0 and ln f = 1 in every window.
+ * Arguments as in rewl_params.  *out receives the handle (NULL on error).
+ * Errors: REWL_ERR_ARG (a parameter out of range, W < 8 bins, or a lattice too
+ * large for one CTA's shared memory), REWL_ERR_NOMEM, REWL_ERR_CUDA,
+ * REWL_ERR_STATE (a walker could not reach its window within the bounded
+ * number of entry moves). */
+rewl_status rewl_create(int q, int L, int h, double overlap, int m, double lnf_final,
+                        double flatness, long long exchange_interval,
+                        unsigned long long seed, rewl_t *out);
+
+/* As rewl_create, from a parameter struct.  spin_bits: 0 picks 4 bits when
+ * q <= 16 and 8 bits otherwise; 4 or 8 force the packing. */
+rewl_status rewl_create_ext(const rewl_params *params, int spin_bits, rewl_t *out);
+
+/* Queue subsequent work of the handle on `stream` (a cudaStream_t passed as
+ * void*; NULL selects the handle's own stream).  The stream must belong to the
+ * handle's device and outlive its use by the handle. */
+rewl_status rewl_set_stream(rewl_t h, void *stream);
+
+/* Run exchange rounds (Sec. 2): each round is K WL steps of every walker of
+ * every unfinished window, then the barrier: visited-bin mask, flatness of
+ * every walker, merge + f-reduction of flat windows, replica exchange (Eq. 1)
+ * between windows (a, a+1) with a = round mod 2.  Runs until every window has
+ * ln f < lnf_final, or until max_rounds rounds have been queued
+ * (max_rounds <= 0: no limit).  Rounds after convergence change nothing.
+ * Synchronises the stream; *converged (may be NULL) is 1 once every window is
+ * done.  Errors: REWL_ERR_OVERFLOW, REWL_ERR_CUDA, REWL_ERR_ARG. */
+rewl_status rewl_run(rewl_t h, long long max_rounds, int *converged);
+
+/* Queue exactly `rounds` exchange rounds on the handle's stream and return
+ * without synchronising (for timing with events on that stream).  Status
+ * flags are checked by the next synchronising call. */
+rewl_status rewl_run_async(rewl_t h, long long rounds);
+
+/* Queue one phase of an exchange round on the handle's stream without
+ * synchronising: REWL_PHASE_SWEEP (K WL steps of every walker of every
+ * unfinished window), REWL_PHASE_CHECK (mask, flatness, merge, f-reduction),
+ * REWL_PHASE_EXCHANGE (replica exchange, then round + 1).  A round is the
+ * three phases in this order; queuing them one by one lets a caller put
+ * timing events between them.  Errors: REWL_ERR_ARG (unknown phase),
+ * REWL_ERR_CUDA (launch failure). */
+enum { REWL_PHASE_SWEEP = 0, REWL_PHASE_CHECK = 1, REWL_PHASE_EXCHANGE = 2 };
+rewl_status rewl_run_phase(rewl_t h, int phase);
+
+/* Synchronise the handle's stream and report its device status:
+ * *converged (may be NULL) as in rewl_run. */
+rewl_status rewl_sync(rewl_t h, int *converged);
+
+/* The joined, normalised ln g over all 2N + 1 bins (Sec. 2, Fig. 2): for each
+ * pair of neighbouring windows the joining bin is the one where the
+ * central-difference slopes of the two pieces agree best; the upper piece is
+ * shifted to meet the lower one there.  Normalised so that sum_E g(E) = q^N.
+ * out: caller-owned host array of len = 2N + 1 doubles; out[b] = ln g(E = b - 2N),
+ * -INFINITY for bins no walker visited.  partial = 0 requires a converged run
+ * (else REWL_ERR_STATE); partial = 1 joins the current estimates. */
+rewl_status rewl_get_lng(rewl_t h, double *out, size_t len, int partial);
+
+/* ln g of window w as held by its walker 0 (W + 1 doubles into `out`, host),
+ * and the window's lowest energy in *e_lo (may be NULL). */
+rewl_status rewl_get_window_lng(rewl_t h, int w, double *out, size_t len, int *e_lo);
+
+/* Sizes of the instance. */
+rewl_status rewl_get_info(rewl_t h, rewl_info *info);
+
+/* Counters of the instance (synchronises the stream). */
+rewl_status rewl_get_stats(rewl_t h, rewl_stats *stats);
+
+/* Copy one state array of the instance to host memory (synchronises):
+ *   REWL_FIELD_SPINS  uint8  [h*m][N]  configuration held by walker g = i*m + k
+ *   REWL_FIELD_ENERGY int32  [h*m]     its energy
+ *   REWL_FIELD_REPLICA uint32 [h*m]    its replica id (initially g)
+ *   REWL_FIELD_STEPS  uint64 [h*m]     WL steps made by walker g
+ *   REWL_FIELD_LNG    double [h*m][W+1] ln g of walker g
+ *   REWL_FIELD_HIST   uint32 [h*m][W+1] H of walker g in the current iteration
+ *   REWL_FIELD_MASK   uint8  [h][W+1]  bins visited by any walker of window i
+ *   REWL_FIELD_LNF    double [h]       ln f of window i
+ *   REWL_FIELD_ITER   int32  [h]       completed iterations of window i
+ *   REWL_FIELD_DONE   uint8  [h]       1 once ln f < lnf_final
+ *   REWL_FIELD_ELO    int32  [h]       lowest energy of window i
+ *   REWL_FIELD_ROUND  int64  [1]       exchange rounds completed
+ * bytes must equal the size above, else REWL_ERR_ARG. */
+enum {
+    REWL_FIELD_SPINS = 0, REWL_FIELD_ENERGY = 1, REWL_FIELD_REPLICA = 2, REWL_FIELD_STEPS = 3,
+    REWL_FIELD_LNG = 4, REWL_FIELD_HIST = 5, REWL_FIELD_MASK = 6, REWL_FIELD_LNF = 7,
+    REWL_FIELD_ITER = 8, REWL_FIELD_DONE = 9, REWL_FIELD_ELO = 10, REWL_FIELD_ROUND = 11
+};
+rewl_status rewl_get_field(rewl_t h, int field, void *out, size_t bytes);
+
+/* Overwrite one state array from host memory (same layouts as rewl_get_field;
+ * REWL_FIELD_SPINS also recounts the energies; REWL_FIELD_ELO and
+ * REWL_FIELD_REPLICA are read-only).  For tests that start from a chosen
+ * state, e.g. fixed weights with ln f = 0. */
+rewl_status rewl_set_field(rewl_t h, int field, const void *in, size_t bytes);
+
+/* Serialise the whole state (at a round boundary) into `buf` (host).  With
+ * buf == NULL only *len is set to the required size.  rewl_load restores it
+ * into a handle created with the same parameters; run(2K) equals
+ * run(K) + save + load + run(K) bit for bit.  Errors: REWL_ERR_ARG (buffer too
+ * small, or a blob of other parameters / corrupted). */
+rewl_status rewl_save(rewl_t h, void *buf, size_t *len);
+rewl_status rewl_load(rewl_t h, const void *buf, size_t len);
+
+/* Release the handle and its device memory.  NULL is ignored. */
+void rewl_destroy(rewl_t h);
+
+/* Message of the last error on this thread ("" if none). */
+const char *rewl_last_error(void);
+
+/* Library version string. */
+const char *rewl_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* REWL_H */

@@ -1,0 +1,11 @@
+"""GB300-native Replica-Exchange Wang-Landau sampling (arXiv:1312.3004) for the
+periodic 2D q-state Potts model.
+
+The computation runs in the CUDA library behind include/rewl.h
+(paper_1312_3004_gb300/_build/librewl.so, built by build.py); this package
+only marshals arguments.
+"""
+from ._lib import RewlError, load  # noqa: F401
+from .rewl import REWL  # noqa: F401
+
+__all__ = ["REWL", "RewlError", "load"]

@@ -1,0 +1,92 @@
+"""ctypes declarations of the C ABI in include/rewl.h (argument marshalling only).
+
+The shared library is the CUDA implementation; there is no CPU fallback.  If
+librewl.so has not been built, load() raises instead of degrading silently.
+"""
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "librewl.so")
+
+REWL_OK = 0
+STATUS_NAMES = {0: "REWL_OK", 1: "REWL_ERR_ARG", 2: "REWL_ERR_NOMEM", 3: "REWL_ERR_CUDA",
+                4: "REWL_ERR_TIMEOUT", 5: "REWL_ERR_OVERFLOW", 6: "REWL_ERR_STATE",
+                7: "REWL_ERR_CANCELLED"}
+
+FIELD_SPINS, FIELD_ENERGY, FIELD_REPLICA, FIELD_STEPS, FIELD_LNG, FIELD_HIST = 0, 1, 2, 3, 4, 5
+PHASE_SWEEP, PHASE_CHECK, PHASE_EXCHANGE = 0, 1, 2
+FIELD_MASK, FIELD_LNF, FIELD_ITER, FIELD_DONE, FIELD_ELO, FIELD_ROUND = 6, 7, 8, 9, 10, 11
+
+
+class RewlError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, str(status)), message))
+        self.status = status
+
+
+class Params(C.Structure):
+    _fields_ = [("q", C.c_int), ("L", C.c_int), ("h", C.c_int), ("overlap", C.c_double),
+                ("m", C.c_int), ("lnf_final", C.c_double), ("flatness", C.c_double),
+                ("exchange_interval", C.c_longlong), ("seed", C.c_ulonglong)]
+
+
+class Info(C.Structure):
+    _fields_ = [("N", C.c_int), ("W", C.c_int), ("walkers", C.c_int), ("spin_bits", C.c_int),
+                ("device_bytes", C.c_size_t)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("rounds", C.c_longlong), ("flips", C.c_longlong), ("accepted", C.c_longlong),
+                ("exch_tried", C.c_longlong), ("exch_accepted", C.c_longlong),
+                ("near_ties", C.c_longlong), ("windows_done", C.c_int), ("converged", C.c_int),
+                ("min_lnf", C.c_double), ("max_lnf", C.c_double)]
+
+
+_lib = None
+
+
+def load():
+    """Load librewl.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("librewl.so is not built (%s); run __graft_entry__.build() first" % LIB_PATH)
+    L = C.CDLL(LIB_PATH)
+    vp, i32, ll, sz, dbl = C.c_void_p, C.c_int, C.c_longlong, C.c_size_t, C.c_double
+    H = C.c_void_p
+    st = C.c_int
+    L.rewl_create.argtypes = [i32, i32, i32, dbl, i32, dbl, dbl, ll, C.c_ulonglong, C.POINTER(H)]
+    L.rewl_create_ext.argtypes = [C.POINTER(Params), i32, C.POINTER(H)]
+    L.rewl_set_stream.argtypes = [H, vp]
+    L.rewl_run.argtypes = [H, ll, C.POINTER(C.c_int)]
+    L.rewl_run_async.argtypes = [H, ll]
+    L.rewl_sync.argtypes = [H, C.POINTER(C.c_int)]
+    L.rewl_run_phase.argtypes = [H, i32]
+    L.rewl_get_lng.argtypes = [H, vp, sz, i32]
+    L.rewl_get_window_lng.argtypes = [H, i32, vp, sz, C.POINTER(C.c_int)]
+    L.rewl_get_info.argtypes = [H, C.POINTER(Info)]
+    L.rewl_get_stats.argtypes = [H, C.POINTER(Stats)]
+    L.rewl_get_field.argtypes = [H, i32, vp, sz]
+    L.rewl_set_field.argtypes = [H, i32, vp, sz]
+    L.rewl_save.argtypes = [H, vp, C.POINTER(sz)]
+    L.rewl_load.argtypes = [H, vp, sz]
+    for name in ("rewl_create", "rewl_create_ext", "rewl_set_stream", "rewl_run", "rewl_run_async",
+                 "rewl_sync", "rewl_run_phase", "rewl_get_lng", "rewl_get_window_lng", "rewl_get_info",
+                 "rewl_get_stats", "rewl_get_field", "rewl_set_field", "rewl_save", "rewl_load"):
+        getattr(L, name).restype = st
+    L.rewl_destroy.argtypes = [H]
+    L.rewl_destroy.restype = None
+    L.rewl_last_error.argtypes = []
+    L.rewl_last_error.restype = C.c_char_p
+    L.rewl_version.argtypes = []
+    L.rewl_version.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def check(status):
+    if status != REWL_OK:
+        msg = load().rewl_last_error().decode("utf-8", "replace")
+        raise RewlError(status, msg)

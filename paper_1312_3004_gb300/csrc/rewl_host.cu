@@ -1,0 +1,598 @@
+// rewl_host.cu -- host driver behind include/rewl.h: parameter checks, the
+// window table, device state, the round loop as a CUDA graph, state access,
+// joining of the windows' pieces (Sec. 2, Fig. 2) and save / load.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "rewl.h"
+#include "rewl_internal.cuh"
+
+using rewl::Ctl;
+using rewl::Model;
+using rewl::State;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+rewl_status fail(rewl_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+#define REWL_CUDA(call)                                                                        \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(REWL_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));        \
+    } while (0)
+
+// Rounds per captured graph: one replay queues this many (sweep, check,
+// exchange) triples; the host polls the completion flag between replays.
+constexpr int kGraphRounds = 8;
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Window table (Sec. 2, Fig. 1): h equal windows of W + 1 bins covering
+// [-2N, 0] with overlap o.  W = ceil(2N / (1 + (h-1)(1-o))); window i starts
+// at -2N + round_half_up(i (2N - W) / (h - 1)).
+bool window_geometry(int L, int h, double o, std::vector<int32_t> &e_lo, int &W) {
+    const long long N = (long long)L * L, R = 2 * N;
+    const double span = 1.0 + (double)(h - 1) * (1.0 - o);
+    long long w = (long long)std::ceil((double)R / span);
+    if (w > R) w = R;
+    if (w < 8) return false;
+    e_lo.assign((size_t)h, 0);
+    for (int i = 0; i < h; ++i) {
+        const long long off = h > 1 ? (2LL * i * (R - w) + (h - 1)) / (2LL * (h - 1)) : 0LL;
+        e_lo[(size_t)i] = (int32_t)(-2 * N + off);
+    }
+    W = (int)w;
+    return true;
+}
+
+}  // namespace
+
+struct rewl_s {
+    rewl_params prm{};
+    Model M{};
+    State S{};
+    rewl::SweepPlan plan{};
+    int device = 0;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    void *dmem = nullptr;
+    size_t dbytes = 0;
+    Ctl *h_ctl = nullptr;  // pinned mirror of the device control block
+    std::vector<int32_t> e_lo;
+    cudaGraphExec_t graph = nullptr;
+    // byte offsets of the state arrays inside dmem (for save / load)
+    struct Part { size_t off, bytes; };
+    std::vector<Part> parts;
+};
+
+namespace {
+
+rewl_status check_params(const rewl_params &p, int spin_bits) {
+    if (p.q < 2 || p.q > 255) return fail(REWL_ERR_ARG, "q=%d outside [2, 255]", p.q);
+    if (p.L < 3 || p.L > 1024) return fail(REWL_ERR_ARG, "L=%d outside [3, 1024]", p.L);
+    if (p.h < 1) return fail(REWL_ERR_ARG, "h=%d < 1", p.h);
+    if (!(p.overlap >= 0.0 && p.overlap < 1.0)) return fail(REWL_ERR_ARG, "overlap %g outside [0, 1)", p.overlap);
+    if (p.m < 1 || p.m > 256) return fail(REWL_ERR_ARG, "m=%d outside [1, 256]", p.m);
+    if (!(p.lnf_final > 0.0 && p.lnf_final < 1.0)) return fail(REWL_ERR_ARG, "lnf_final %g outside (0, 1)", p.lnf_final);
+    if (!(p.flatness > 0.0 && p.flatness < 1.0)) return fail(REWL_ERR_ARG, "flatness %g outside (0, 1)", p.flatness);
+    if (p.exchange_interval < 1) return fail(REWL_ERR_ARG, "exchange_interval %lld < 1", p.exchange_interval);
+    if (spin_bits != 0 && spin_bits != 4 && spin_bits != 8) return fail(REWL_ERR_ARG, "spin_bits %d not 0, 4 or 8", spin_bits);
+    if (spin_bits == 4 && p.q > 16) return fail(REWL_ERR_ARG, "4-bit spins need q <= 16");
+    if ((long long)p.h * p.m > (1LL << 30)) return fail(REWL_ERR_ARG, "too many walkers");
+    return REWL_OK;
+}
+
+rewl_status enqueue_round(rewl_s *h, cudaStream_t s) {
+    REWL_CUDA(rewl::launch_sweep(h->M, h->S, h->plan, s));
+    REWL_CUDA(rewl::launch_window_check(h->M, h->S, s));
+    REWL_CUDA(rewl::launch_exchange(h->M, h->S, s));
+    return REWL_OK;
+}
+
+rewl_status build_graph(rewl_s *h) {
+    cudaStream_t cap;
+    REWL_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    rewl_status st = REWL_OK;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        for (int r = 0; r < kGraphRounds && st == REWL_OK; ++r) st = enqueue_round(h, cap);
+        e = cudaStreamEndCapture(cap, &graph);
+    }
+    if (e == cudaSuccess && st == REWL_OK) e = cudaGraphInstantiate(&h->graph, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cap);
+    if (st != REWL_OK) return st;
+    if (e != cudaSuccess) return fail(REWL_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    return REWL_OK;
+}
+
+rewl_status enqueue_rounds(rewl_s *h, long long n) {
+    while (n >= kGraphRounds) {
+        REWL_CUDA(cudaGraphLaunch(h->graph, h->stream));
+        n -= kGraphRounds;
+    }
+    for (; n > 0; --n) {
+        rewl_status st = enqueue_round(h, h->stream);
+        if (st) return st;
+    }
+    return REWL_OK;
+}
+
+rewl_status read_ctl(rewl_s *h) {
+    REWL_CUDA(cudaMemcpyAsync(h->h_ctl, h->S.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
+    REWL_CUDA(cudaStreamSynchronize(h->stream));
+    if (h->h_ctl->error & rewl::ERR_OVERFLOW) return fail(REWL_ERR_OVERFLOW, "a histogram bin reached 2^31 visits");
+    if (h->h_ctl->error & rewl::ERR_ENTRY) return fail(REWL_ERR_STATE, "a walker could not enter its window");
+    return REWL_OK;
+}
+
+// ---- joining (Sec. 2, Fig. 2) ------------------------------------------------
+// Slope of a piece at local bin i: difference quotient between the nearest
+// visited bins below and above i (i itself must be visited).
+bool piece_slope(const double *lg, const uint8_t *vis, int B, int i, double *beta) {
+    if (!vis[i]) return false;
+    int a = i - 1;
+    while (a >= 0 && !vis[a]) --a;
+    int b = i + 1;
+    while (b < B && !vis[b]) ++b;
+    if (a < 0 || b >= B) return false;
+    *beta = (lg[b] - lg[a]) / (double)(b - a);
+    return true;
+}
+
+rewl_status join_windows(int N, int W, const std::vector<int32_t> &e_lo, const std::vector<double> &lw,
+                         const std::vector<uint8_t> &mw, double *out) {
+    const int h = (int)e_lo.size(), B = W + 1, nb = 2 * N + 1;
+    std::vector<double> offset((size_t)h, 0.0);
+    std::vector<int> cut((size_t)h, 0);
+    int last = -1;
+    for (int a = 0; a + 1 < h; ++a) {
+        const int lo_a = e_lo[(size_t)a] + 2 * N, lo_b = e_lo[(size_t)a + 1] + 2 * N;
+        const double *pa = &lw[(size_t)a * B], *pb = &lw[(size_t)(a + 1) * B];
+        const uint8_t *va = &mw[(size_t)a * B], *vb = &mw[(size_t)(a + 1) * B];
+        int join = -1;
+        double gap = 0.0;
+        for (int b = std::max(lo_b, last + 1); b <= lo_a + W; ++b) {
+            double ba, bb;
+            if (!piece_slope(pa, va, B, b - lo_a, &ba) || !piece_slope(pb, vb, B, b - lo_b, &bb)) continue;
+            const double d = std::fabs(ba - bb);
+            if (join < 0 || d < gap) {
+                join = b;
+                gap = d;
+            }
+        }
+        if (join < 0) return fail(REWL_ERR_STATE, "windows %d and %d have no common joining bin", a, a + 1);
+        offset[(size_t)a + 1] = (pa[join - lo_a] + offset[(size_t)a]) - pb[join - lo_b];
+        cut[(size_t)a] = join;
+        last = join;
+    }
+    for (int b = 0; b < nb; ++b) out[b] = -INFINITY;
+    for (int a = 0; a < h; ++a) {
+        const int lo = e_lo[(size_t)a] + 2 * N;
+        const int first = a == 0 ? lo : cut[(size_t)a - 1] + 1;
+        const int end = a == h - 1 ? lo + W : cut[(size_t)a];
+        for (int b = first; b <= end; ++b)
+            if (mw[(size_t)a * B + (b - lo)]) out[b] = lw[(size_t)a * B + (b - lo)] + offset[(size_t)a];
+    }
+    return REWL_OK;
+}
+
+// Shift so that sum over visited bins of g(E) = q^N.
+void normalise_total(int q, int N, double *v, int nb) {
+    double top = -INFINITY;
+    for (int b = 0; b < nb; ++b) top = v[b] > top ? v[b] : top;
+    if (top == -INFINITY) return;
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b)
+        if (v[b] != -INFINITY) s += std::exp(v[b] - top);
+    const double shift = (double)N * std::log((double)q) - (top + std::log(s));
+    for (int b = 0; b < nb; ++b)
+        if (v[b] != -INFINITY) v[b] += shift;
+}
+
+uint64_t fnv1a(const unsigned char *p, size_t n, uint64_t hsh = 1469598103934665603ull) {
+    for (size_t i = 0; i < n; ++i) {
+        hsh ^= p[i];
+        hsh *= 1099511628211ull;
+    }
+    return hsh;
+}
+
+bool same_params(const rewl_params &a, const rewl_params &b) {
+    return a.q == b.q && a.L == b.L && a.h == b.h && a.overlap == b.overlap && a.m == b.m &&
+           a.lnf_final == b.lnf_final && a.flatness == b.flatness && a.exchange_interval == b.exchange_interval &&
+           a.seed == b.seed;
+}
+
+struct SaveHeader {
+    char magic[8];
+    uint32_t version;
+    uint32_t spin_bits;
+    rewl_params prm;
+    uint64_t payload;
+    uint64_t checksum;
+};
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+const char *rewl_last_error(void) { return g_last_error.c_str(); }
+
+const char *rewl_version(void) { return "rewl-gb300 0.1 (sm_103a)"; }
+
+rewl_status rewl_create_ext(const rewl_params *prm, int spin_bits, rewl_t *out) {
+    if (!prm || !out) return fail(REWL_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    rewl_status st = check_params(*prm, spin_bits);
+    if (st) return st;
+    std::vector<int32_t> e_lo;
+    int W = 0;
+    if (!window_geometry(prm->L, prm->h, prm->overlap, e_lo, W))
+        return fail(REWL_ERR_ARG, "window width below 8 bins (L=%d, h=%d, overlap=%g)", prm->L, prm->h, prm->overlap);
+
+    rewl_s *h = new rewl_s();
+    h->prm = *prm;
+    h->e_lo = e_lo;
+    Model &M = h->M;
+    M.q = prm->q;
+    M.L = prm->L;
+    M.N = prm->L * prm->L;
+    M.W = W;
+    M.B = W + 1;
+    M.h = prm->h;
+    M.m = prm->m;
+    M.G = prm->h * prm->m;
+    M.bits = spin_bits ? spin_bits : (prm->q <= 16 ? 4 : 8);
+    M.wpc = (M.N * M.bits + 31) / 32;
+    M.key0 = (uint32_t)(prm->seed & 0xffffffffull);
+    M.key1 = (uint32_t)(prm->seed >> 32);
+    M.divL = (uint32_t)((0x100000000ull + (unsigned long long)prm->L - 1) / (unsigned long long)prm->L);
+    M.K = prm->exchange_interval;
+    M.lnf_final = prm->lnf_final;
+    M.flatness = prm->flatness;
+
+    auto cleanup = [&](rewl_status s) {
+        rewl_destroy(h);
+        return s;
+    };
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) return cleanup(fail(REWL_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e)));
+    int sms = 0, optin = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+    if (rewl::sweep_smem_per_walker(M) > (size_t)optin)
+        return cleanup(fail(REWL_ERR_ARG, "one walker needs %zu bytes of shared memory (> %d)",
+                            rewl::sweep_smem_per_walker(M), optin));
+    h->plan = rewl::plan_sweep(M, sms, (size_t)optin);
+
+    // one allocation, carved into 256-byte aligned arrays
+    const size_t G = (size_t)M.G, B = (size_t)M.B, hh = (size_t)M.h;
+    const size_t sizes[] = {G * M.wpc * 4, G * 4, G * 4, G * 8, G * B * 8, G * B * 4, hh * B, hh * 4, hh * 8, hh * 4, hh,
+                            sizeof(Ctl)};
+    size_t off = 0;
+    for (size_t s : sizes) {
+        h->parts.push_back({off, s});
+        off += align256(s);
+    }
+    h->dbytes = off;
+    e = cudaMalloc(&h->dmem, off);
+    if (e != cudaSuccess) return cleanup(fail(REWL_ERR_NOMEM, "cudaMalloc(%zu): %s", off, cudaGetErrorString(e)));
+    auto at = [&](int i) { return (void *)((char *)h->dmem + h->parts[(size_t)i].off); };
+    State &S = h->S;
+    S.spins = (uint32_t *)at(0);
+    S.cfg_E = (int32_t *)at(1);
+    S.slot_cfg = (uint32_t *)at(2);
+    S.t = (unsigned long long *)at(3);
+    S.lng = (double *)at(4);
+    S.H = (uint32_t *)at(5);
+    S.mask = (uint8_t *)at(6);
+    S.e_lo = (int32_t *)at(7);
+    S.lnf = (double *)at(8);
+    S.iter = (int32_t *)at(9);
+    S.done = (uint8_t *)at(10);
+    S.ctl = (Ctl *)at(11);
+
+    e = cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cleanup(fail(REWL_ERR_CUDA, "stream: %s", cudaGetErrorString(e)));
+    h->stream = h->own_stream;
+    e = cudaMallocHost(&h->h_ctl, sizeof(Ctl));
+    if (e != cudaSuccess) return cleanup(fail(REWL_ERR_NOMEM, "cudaMallocHost: %s", cudaGetErrorString(e)));
+
+    std::vector<double> lnf0(hh, 1.0);  // ln f_0 = 1
+    e = cudaMemsetAsync(h->dmem, 0, off, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(S.e_lo, e_lo.data(), hh * 4, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(S.lnf, lnf0.data(), hh * 8, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = rewl::launch_init(M, S, h->stream);
+    if (e == cudaSuccess) e = rewl::prepare_sweep(M, h->plan);
+    if (e != cudaSuccess) return cleanup(fail(REWL_ERR_CUDA, "initialisation: %s", cudaGetErrorString(e)));
+    st = read_ctl(h);
+    if (st) return cleanup(st);
+    st = build_graph(h);
+    if (st) return cleanup(st);
+    *out = h;
+    return REWL_OK;
+}
+
+rewl_status rewl_create(int q, int L, int h, double overlap, int m, double lnf_final, double flatness,
+                        long long exchange_interval, unsigned long long seed, rewl_t *out) {
+    rewl_params p;
+    p.q = q;
+    p.L = L;
+    p.h = h;
+    p.overlap = overlap;
+    p.m = m;
+    p.lnf_final = lnf_final;
+    p.flatness = flatness;
+    p.exchange_interval = exchange_interval;
+    p.seed = seed;
+    return rewl_create_ext(&p, 0, out);
+}
+
+void rewl_destroy(rewl_t h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    if (h->own_stream) cudaStreamDestroy(h->own_stream);
+    if (h->h_ctl) cudaFreeHost(h->h_ctl);
+    if (h->dmem) cudaFree(h->dmem);
+    delete h;
+}
+
+rewl_status rewl_set_stream(rewl_t h, void *stream) {
+    if (!h) return fail(REWL_ERR_ARG, "NULL handle");
+    REWL_CUDA(cudaStreamSynchronize(h->stream));
+    h->stream = stream ? (cudaStream_t)stream : h->own_stream;
+    return REWL_OK;
+}
+
+rewl_status rewl_run_async(rewl_t h, long long rounds) {
+    if (!h) return fail(REWL_ERR_ARG, "NULL handle");
+    if (rounds < 0) return fail(REWL_ERR_ARG, "rounds < 0");
+    return enqueue_rounds(h, rounds);
+}
+
+rewl_status rewl_run_phase(rewl_t h, int phase) {
+    if (!h) return fail(REWL_ERR_ARG, "NULL handle");
+    switch (phase) {
+    case REWL_PHASE_SWEEP: REWL_CUDA(rewl::launch_sweep(h->M, h->S, h->plan, h->stream)); break;
+    case REWL_PHASE_CHECK: REWL_CUDA(rewl::launch_window_check(h->M, h->S, h->stream)); break;
+    case REWL_PHASE_EXCHANGE: REWL_CUDA(rewl::launch_exchange(h->M, h->S, h->stream)); break;
+    default: return fail(REWL_ERR_ARG, "unknown phase %d", phase);
+    }
+    return REWL_OK;
+}
+
+rewl_status rewl_sync(rewl_t h, int *converged) {
+    if (!h) return fail(REWL_ERR_ARG, "NULL handle");
+    rewl_status st = read_ctl(h);
+    if (converged) *converged = h->h_ctl->all_done ? 1 : 0;
+    return st;
+}
+
+rewl_status rewl_run(rewl_t h, long long max_rounds, int *converged) {
+    if (!h) return fail(REWL_ERR_ARG, "NULL handle");
+    long long left = max_rounds;
+    rewl_status st = read_ctl(h);
+    while (st == REWL_OK && !h->h_ctl->all_done && (max_rounds <= 0 || left > 0)) {
+        const long long n = (max_rounds <= 0 || left >= kGraphRounds) ? kGraphRounds : left;
+        st = enqueue_rounds(h, n);
+        if (st == REWL_OK) st = read_ctl(h);
+        left -= n;
+    }
+    if (converged) *converged = h->h_ctl->all_done ? 1 : 0;
+    return st;
+}
+
+rewl_status rewl_get_window_lng(rewl_t h, int w, double *out, size_t len, int *e_lo) {
+    if (!h || !out) return fail(REWL_ERR_ARG, "NULL argument");
+    if (w < 0 || w >= h->M.h) return fail(REWL_ERR_ARG, "window %d outside [0, %d)", w, h->M.h);
+    if (len != (size_t)h->M.B) return fail(REWL_ERR_ARG, "len %zu != W + 1 = %d", len, h->M.B);
+    REWL_CUDA(cudaMemcpyAsync(out, h->S.lng + (size_t)w * h->M.m * h->M.B, len * 8, cudaMemcpyDeviceToHost, h->stream));
+    REWL_CUDA(cudaStreamSynchronize(h->stream));
+    if (e_lo) *e_lo = h->e_lo[(size_t)w];
+    return REWL_OK;
+}
+
+rewl_status rewl_get_lng(rewl_t h, double *out, size_t len, int partial) {
+    if (!h || !out) return fail(REWL_ERR_ARG, "NULL argument");
+    const Model &M = h->M;
+    if (len != (size_t)(2 * M.N + 1)) return fail(REWL_ERR_ARG, "len %zu != 2N + 1 = %d", len, 2 * M.N + 1);
+    rewl_status st = read_ctl(h);
+    if (st) return st;
+    if (!partial && !h->h_ctl->all_done) return fail(REWL_ERR_STATE, "run has not converged");
+    std::vector<double> lw((size_t)M.h * M.B);
+    std::vector<uint8_t> mw((size_t)M.h * M.B);
+    // walker 0 of every window: rows w*m of the [G][B] ln g array
+    REWL_CUDA(cudaMemcpy2DAsync(lw.data(), (size_t)M.B * 8, h->S.lng, (size_t)M.m * M.B * 8, (size_t)M.B * 8, (size_t)M.h,
+                                cudaMemcpyDeviceToHost, h->stream));
+    REWL_CUDA(cudaMemcpyAsync(mw.data(), h->S.mask, mw.size(), cudaMemcpyDeviceToHost, h->stream));
+    REWL_CUDA(cudaStreamSynchronize(h->stream));
+    st = join_windows(M.N, M.W, h->e_lo, lw, mw, out);
+    if (st) return st;
+    normalise_total(M.q, M.N, out, 2 * M.N + 1);
+    return REWL_OK;
+}
+
+rewl_status rewl_get_info(rewl_t h, rewl_info *info) {
+    if (!h || !info) return fail(REWL_ERR_ARG, "NULL argument");
+    info->N = h->M.N;
+    info->W = h->M.W;
+    info->walkers = h->M.G;
+    info->spin_bits = h->M.bits;
+    info->device_bytes = h->dbytes;
+    return REWL_OK;
+}
+
+rewl_status rewl_get_stats(rewl_t h, rewl_stats *s) {
+    if (!h || !s) return fail(REWL_ERR_ARG, "NULL argument");
+    std::vector<double> lnf((size_t)h->M.h);
+    std::vector<uint8_t> done((size_t)h->M.h);
+    REWL_CUDA(cudaMemcpyAsync(lnf.data(), h->S.lnf, lnf.size() * 8, cudaMemcpyDeviceToHost, h->stream));
+    REWL_CUDA(cudaMemcpyAsync(done.data(), h->S.done, done.size(), cudaMemcpyDeviceToHost, h->stream));
+    rewl_status st = read_ctl(h);
+    const Ctl &c = *h->h_ctl;
+    s->rounds = (long long)c.round;
+    s->flips = (long long)c.flips;
+    s->accepted = (long long)c.accepted;
+    s->exch_tried = (long long)c.xtried;
+    s->exch_accepted = (long long)c.xacc;
+    s->near_ties = (long long)c.ties;
+    s->windows_done = 0;
+    s->min_lnf = INFINITY;
+    s->max_lnf = -INFINITY;
+    for (size_t i = 0; i < done.size(); ++i) {
+        s->windows_done += done[i] ? 1 : 0;
+        s->min_lnf = std::min(s->min_lnf, lnf[i]);
+        s->max_lnf = std::max(s->max_lnf, lnf[i]);
+    }
+    s->converged = c.all_done ? 1 : 0;
+    return st;
+}
+
+static rewl_status field_geometry(rewl_t h, int field, void **dev, size_t *bytes) {
+    const size_t G = (size_t)h->M.G, B = (size_t)h->M.B, hh = (size_t)h->M.h;
+    switch (field) {
+    case REWL_FIELD_SPINS: *dev = nullptr; *bytes = G * (size_t)h->M.N; break;
+    case REWL_FIELD_ENERGY: *dev = nullptr; *bytes = G * 4; break;
+    case REWL_FIELD_REPLICA: *dev = h->S.slot_cfg; *bytes = G * 4; break;
+    case REWL_FIELD_STEPS: *dev = h->S.t; *bytes = G * 8; break;
+    case REWL_FIELD_LNG: *dev = h->S.lng; *bytes = G * B * 8; break;
+    case REWL_FIELD_HIST: *dev = h->S.H; *bytes = G * B * 4; break;
+    case REWL_FIELD_MASK: *dev = h->S.mask; *bytes = hh * B; break;
+    case REWL_FIELD_LNF: *dev = h->S.lnf; *bytes = hh * 8; break;
+    case REWL_FIELD_ITER: *dev = h->S.iter; *bytes = hh * 4; break;
+    case REWL_FIELD_DONE: *dev = h->S.done; *bytes = hh; break;
+    case REWL_FIELD_ELO: *dev = h->S.e_lo; *bytes = hh * 4; break;
+    case REWL_FIELD_ROUND: *dev = &h->S.ctl->round; *bytes = 8; break;
+    default: return fail(REWL_ERR_ARG, "unknown field %d", field);
+    }
+    return REWL_OK;
+}
+
+rewl_status rewl_get_field(rewl_t h, int field, void *out, size_t bytes) {
+    if (!h || !out) return fail(REWL_ERR_ARG, "NULL argument");
+    void *dev;
+    size_t need;
+    rewl_status st = field_geometry(h, field, &dev, &need);
+    if (st) return st;
+    if (bytes != need) return fail(REWL_ERR_ARG, "field %d needs %zu bytes, got %zu", field, need, bytes);
+    if (field == REWL_FIELD_SPINS) {
+        uint8_t *tmp = nullptr;
+        REWL_CUDA(cudaMallocAsync((void **)&tmp, need, h->stream));
+        cudaError_t e = rewl::launch_get_spins(h->M, h->S, tmp, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, need, cudaMemcpyDeviceToHost, h->stream);
+        cudaFreeAsync(tmp, h->stream);
+        if (e != cudaSuccess) return fail(REWL_ERR_CUDA, "spins: %s", cudaGetErrorString(e));
+    } else if (field == REWL_FIELD_ENERGY) {
+        std::vector<uint32_t> slot((size_t)h->M.G);
+        std::vector<int32_t> cfgE((size_t)h->M.G);
+        REWL_CUDA(cudaMemcpyAsync(slot.data(), h->S.slot_cfg, slot.size() * 4, cudaMemcpyDeviceToHost, h->stream));
+        REWL_CUDA(cudaMemcpyAsync(cfgE.data(), h->S.cfg_E, cfgE.size() * 4, cudaMemcpyDeviceToHost, h->stream));
+        REWL_CUDA(cudaStreamSynchronize(h->stream));
+        int32_t *o = (int32_t *)out;
+        for (size_t g = 0; g < slot.size(); ++g) o[g] = cfgE[slot[g]];
+        return REWL_OK;
+    } else {
+        REWL_CUDA(cudaMemcpyAsync(out, dev, need, cudaMemcpyDeviceToHost, h->stream));
+    }
+    REWL_CUDA(cudaStreamSynchronize(h->stream));
+    return REWL_OK;
+}
+
+rewl_status rewl_set_field(rewl_t h, int field, const void *in, size_t bytes) {
+    if (!h || !in) return fail(REWL_ERR_ARG, "NULL argument");
+    if (field == REWL_FIELD_ELO || field == REWL_FIELD_REPLICA || field == REWL_FIELD_ENERGY)
+        return fail(REWL_ERR_ARG, "field %d is read-only", field);
+    void *dev;
+    size_t need;
+    rewl_status st = field_geometry(h, field, &dev, &need);
+    if (st) return st;
+    if (bytes != need) return fail(REWL_ERR_ARG, "field %d needs %zu bytes, got %zu", field, need, bytes);
+    if (field == REWL_FIELD_SPINS) {
+        const uint8_t *s = (const uint8_t *)in;
+        for (size_t i = 0; i < need; ++i)
+            if (s[i] >= h->M.q) return fail(REWL_ERR_ARG, "spin value %d >= q", (int)s[i]);
+        uint8_t *tmp = nullptr;
+        REWL_CUDA(cudaMallocAsync((void **)&tmp, need, h->stream));
+        cudaError_t e = cudaMemcpyAsync(tmp, in, need, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = rewl::launch_set_spins(h->M, h->S, tmp, h->stream);
+        cudaFreeAsync(tmp, h->stream);
+        if (e != cudaSuccess) return fail(REWL_ERR_CUDA, "spins: %s", cudaGetErrorString(e));
+    } else {
+        REWL_CUDA(cudaMemcpyAsync(dev, in, need, cudaMemcpyHostToDevice, h->stream));
+    }
+    REWL_CUDA(cudaStreamSynchronize(h->stream));
+    return REWL_OK;
+}
+
+rewl_status rewl_save(rewl_t h, void *buf, size_t *len) {
+    if (!h || !len) return fail(REWL_ERR_ARG, "NULL argument");
+    size_t payload = 0;
+    for (auto &p : h->parts) payload += p.bytes;
+    const size_t need = sizeof(SaveHeader) + payload;
+    if (!buf) {
+        *len = need;
+        return REWL_OK;
+    }
+    if (*len < need) return fail(REWL_ERR_ARG, "buffer of %zu bytes < %zu", *len, need);
+    unsigned char *dst = (unsigned char *)buf + sizeof(SaveHeader);
+    for (auto &p : h->parts) {
+        REWL_CUDA(cudaMemcpyAsync(dst, (char *)h->dmem + p.off, p.bytes, cudaMemcpyDeviceToHost, h->stream));
+        dst += p.bytes;
+    }
+    REWL_CUDA(cudaStreamSynchronize(h->stream));
+    SaveHeader hd;
+    std::memset(&hd, 0, sizeof hd);
+    std::memcpy(hd.magic, "REWLSAV1", 8);
+    hd.version = 1;
+    hd.spin_bits = (uint32_t)h->M.bits;
+    hd.prm = h->prm;
+    hd.payload = payload;
+    hd.checksum = fnv1a((const unsigned char *)buf + sizeof(SaveHeader), payload);
+    std::memcpy(buf, &hd, sizeof hd);
+    *len = need;
+    return REWL_OK;
+}
+
+rewl_status rewl_load(rewl_t h, const void *buf, size_t len) {
+    if (!h || !buf) return fail(REWL_ERR_ARG, "NULL argument");
+    if (len < sizeof(SaveHeader)) return fail(REWL_ERR_ARG, "blob too short");
+    SaveHeader hd;
+    std::memcpy(&hd, buf, sizeof hd);
+    size_t payload = 0;
+    for (auto &p : h->parts) payload += p.bytes;
+    if (std::memcmp(hd.magic, "REWLSAV1", 8) != 0 || hd.version != 1) return fail(REWL_ERR_ARG, "not a rewl state blob");
+    if (hd.payload != payload || len != sizeof(SaveHeader) + payload || hd.spin_bits != (uint32_t)h->M.bits ||
+        !same_params(hd.prm, h->prm))
+        return fail(REWL_ERR_ARG, "blob belongs to an instance with other parameters");
+    if (fnv1a((const unsigned char *)buf + sizeof(SaveHeader), payload) != hd.checksum)
+        return fail(REWL_ERR_ARG, "blob checksum mismatch (corrupted)");
+    const unsigned char *src = (const unsigned char *)buf + sizeof(SaveHeader);
+    for (auto &p : h->parts) {
+        REWL_CUDA(cudaMemcpyAsync((char *)h->dmem + p.off, src, p.bytes, cudaMemcpyHostToDevice, h->stream));
+        src += p.bytes;
+    }
+    REWL_CUDA(cudaStreamSynchronize(h->stream));
+    return read_ctl(h);
+}
+
+}  // extern "C"

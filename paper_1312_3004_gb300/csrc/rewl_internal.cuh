@@ -1,0 +1,80 @@
+// rewl_internal.cuh -- device state layout and kernel launchers shared by the
+// kernels (rewl_kernels.cu) and the host driver (rewl_host.cu).
+//
+// Device state of one REWL instance (Sec. 2 of arXiv:1312.3004): h windows of
+// m walkers, G = h*m walker slots, C = G configuration buffers.  A walker slot
+// g = i*m + k owns ln g and H of window i; the configuration it carries is the
+// buffer slot_cfg[g], so a replica exchange swaps two 32-bit buffer ids instead
+// of two lattices, and the buffer id doubles as the replica id.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rewl {
+
+// Device control block: round counter, completion and error flags, counters.
+struct Ctl {
+    unsigned long long round;     // exchange rounds completed
+    unsigned int all_done;        // every window has ln f < ln f_final
+    unsigned int error;           // ERR_* bits
+    unsigned long long flips;     // WL proposals
+    unsigned long long accepted;  // accepted WL proposals
+    unsigned long long xtried;    // exchange pairs evaluated
+    unsigned long long xacc;      // exchanges carried out
+    unsigned long long ties;      // |u - exp(D)| < 1e-14 acceptance draws
+    unsigned long long slow;      // WL decisions resolved on the FP64 path
+};
+
+enum : unsigned int {
+    ERR_OVERFLOW = 1u,  // an H bin reached 2^31
+    ERR_ENTRY = 2u,     // a walker could not reach its window
+};
+
+// Random-number domains: the fourth Philox counter word.
+enum : uint32_t { DOM_WL = 0, DOM_INIT = 1, DOM_ENTRY = 2, DOM_PERM = 3, DOM_XACC = 4 };
+
+struct Model {
+    int q, L, N, W, B;        // B = W + 1 bins per window
+    int h, m, G;              // windows, walkers per window, walker slots
+    int bits;                 // 4 or 8 bits per stored spin
+    int wpc;                  // 32-bit words per configuration buffer
+    uint32_t key0, key1;      // Philox key = seed
+    uint32_t divL;            // ceil(2^32 / L) for site -> (x, y)
+    long long K;              // WL steps per walker between exchanges
+    double lnf_final, flatness;
+};
+
+struct State {
+    uint32_t *spins;      // [G][wpc] packed configurations, by buffer id
+    int32_t *cfg_E;       // [G] energy of each configuration buffer
+    uint32_t *slot_cfg;   // [G] buffer held by walker slot g (its replica id)
+    unsigned long long *t;// [G] WL steps of walker slot g
+    double *lng;          // [G][B] ln g of walker slot g
+    uint32_t *H;          // [G][B] histogram of walker slot g
+    uint8_t *mask;        // [h][B] bins visited by any walker of the window
+    int32_t *e_lo;        // [h] lowest energy of each window
+    double *lnf;          // [h] ln f of each window
+    int32_t *iter;        // [h] completed iterations
+    uint8_t *done;        // [h] window finished
+    Ctl *ctl;             // control block
+};
+
+struct SweepPlan {
+    int P;           // walkers per CTA
+    int threads;     // CTA size
+    int grid;        // CTAs
+    size_t smem;     // dynamic shared memory bytes
+};
+
+// Launchers (rewl_kernels.cu).  All enqueue on `s` and return the launch error.
+cudaError_t launch_init(const Model &M, const State &S, cudaStream_t s);
+SweepPlan plan_sweep(const Model &M, int num_sms, size_t smem_optin);
+cudaError_t prepare_sweep(const Model &M, const SweepPlan &p);
+cudaError_t launch_sweep(const Model &M, const State &S, const SweepPlan &p, cudaStream_t s);
+cudaError_t launch_window_check(const Model &M, const State &S, cudaStream_t s);
+cudaError_t launch_exchange(const Model &M, const State &S, cudaStream_t s);
+cudaError_t launch_set_spins(const Model &M, const State &S, const uint8_t *spins_dev, cudaStream_t s);
+cudaError_t launch_get_spins(const Model &M, const State &S, uint8_t *spins_dev, cudaStream_t s);
+size_t sweep_smem_per_walker(const Model &M);
+
+}  // namespace rewl

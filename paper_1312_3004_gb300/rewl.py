@@ -1,0 +1,133 @@
+"""Python handle over the C ABI (include/rewl.h).
+
+Marshalling only: every step of REWL (arXiv:1312.3004, Sec. 2) runs in the
+CUDA library.  Host results come back as numpy arrays.
+"""
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import check
+
+_FIELD_DTYPES = {
+    _lib.FIELD_SPINS: np.uint8, _lib.FIELD_ENERGY: np.int32, _lib.FIELD_REPLICA: np.uint32,
+    _lib.FIELD_STEPS: np.uint64, _lib.FIELD_LNG: np.float64, _lib.FIELD_HIST: np.uint32,
+    _lib.FIELD_MASK: np.uint8, _lib.FIELD_LNF: np.float64, _lib.FIELD_ITER: np.int32,
+    _lib.FIELD_DONE: np.uint8, _lib.FIELD_ELO: np.int32, _lib.FIELD_ROUND: np.int64,
+}
+FIELDS = {"spins": _lib.FIELD_SPINS, "energy": _lib.FIELD_ENERGY, "replica": _lib.FIELD_REPLICA,
+          "steps": _lib.FIELD_STEPS, "lng": _lib.FIELD_LNG, "hist": _lib.FIELD_HIST,
+          "mask": _lib.FIELD_MASK, "lnf": _lib.FIELD_LNF, "iter": _lib.FIELD_ITER,
+          "done": _lib.FIELD_DONE, "e_lo": _lib.FIELD_ELO, "round": _lib.FIELD_ROUND}
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class REWL:
+    """One REWL instance on the current CUDA device.
+
+    Parameters follow Sec. 2: q-state Potts on an L x L torus, h windows with
+    overlap o, m walkers per window, stop at ln f < lnf_final, flatness p,
+    K = exchange_interval WL steps per walker between exchanges, Philox seed.
+    """
+
+    def __init__(self, q, L, h, overlap, m, lnf_final, flatness, exchange_interval, seed,
+                 spin_bits=0, stream=None):
+        self._L = _lib.load()
+        self._h = C.c_void_p()
+        p = _lib.Params(q, L, h, overlap, m, lnf_final, flatness, exchange_interval, seed)
+        check(self._L.rewl_create_ext(C.byref(p), spin_bits, C.byref(self._h)))
+        info = _lib.Info()
+        check(self._L.rewl_get_info(self._h, C.byref(info)))
+        self.q, self.L, self.h, self.m = q, L, h, m
+        self.N, self.W, self.G = info.N, info.W, info.walkers
+        self.B = self.W + 1
+        self.spin_bits = info.spin_bits
+        self.device_bytes = info.device_bytes
+        if stream is not None:
+            self.set_stream(stream)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._L.rewl_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None."""
+        raw = getattr(stream, "cuda_stream", stream)
+        check(self._L.rewl_set_stream(self._h, C.c_void_p(raw) if raw else None))
+
+    def run(self, max_rounds=0):
+        conv = C.c_int(0)
+        check(self._L.rewl_run(self._h, max_rounds, C.byref(conv)))
+        return bool(conv.value)
+
+    def run_async(self, rounds):
+        check(self._L.rewl_run_async(self._h, rounds))
+
+    def run_phase(self, phase):
+        """Queue one phase (_lib.PHASE_SWEEP / PHASE_CHECK / PHASE_EXCHANGE)."""
+        check(self._L.rewl_run_phase(self._h, phase))
+
+    def sync(self):
+        conv = C.c_int(0)
+        check(self._L.rewl_sync(self._h, C.byref(conv)))
+        return bool(conv.value)
+
+    def lng(self, partial=False):
+        out = np.zeros(2 * self.N + 1)
+        check(self._L.rewl_get_lng(self._h, _ptr(out), out.size, 1 if partial else 0))
+        return out
+
+    def window_lng(self, w):
+        out = np.zeros(self.B)
+        e = C.c_int(0)
+        check(self._L.rewl_get_window_lng(self._h, w, _ptr(out), out.size, C.byref(e)))
+        return out, e.value
+
+    def stats(self):
+        s = _lib.Stats()
+        check(self._L.rewl_get_stats(self._h, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in _lib.Stats._fields_}
+
+    def _shape(self, field):
+        G, B, h, N = self.G, self.B, self.h, self.N
+        return {_lib.FIELD_SPINS: (G, N), _lib.FIELD_ENERGY: (G,), _lib.FIELD_REPLICA: (G,),
+                _lib.FIELD_STEPS: (G,), _lib.FIELD_LNG: (G, B), _lib.FIELD_HIST: (G, B),
+                _lib.FIELD_MASK: (h, B), _lib.FIELD_LNF: (h,), _lib.FIELD_ITER: (h,),
+                _lib.FIELD_DONE: (h,), _lib.FIELD_ELO: (h,), _lib.FIELD_ROUND: (1,)}[field]
+
+    def get(self, name):
+        f = FIELDS[name]
+        a = np.zeros(self._shape(f), dtype=_FIELD_DTYPES[f])
+        check(self._L.rewl_get_field(self._h, f, _ptr(a), a.nbytes))
+        return a
+
+    def set(self, name, values):
+        f = FIELDS[name]
+        a = np.ascontiguousarray(np.broadcast_to(values, self._shape(f)), dtype=_FIELD_DTYPES[f])
+        check(self._L.rewl_set_field(self._h, f, _ptr(a), a.nbytes))
+
+    @property
+    def round(self):
+        return int(self.get("round")[0])
+
+    def save(self):
+        n = C.c_size_t(0)
+        check(self._L.rewl_save(self._h, None, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        check(self._L.rewl_save(self._h, buf, C.byref(n)))
+        return buf.raw[: n.value]
+
+    def load(self, blob):
+        buf = C.create_string_buffer(bytes(blob), len(blob))
+        check(self._L.rewl_load(self._h, buf, len(blob)))

@@ -1,0 +1,45 @@
+"""Seeded synthetic workloads (parameter sets only; no REWL arithmetic).
+
+The paper's Potts runs (Sec. 3.1) are defined by lattice parameters and seeds;
+there is no dataset.  These named configurations are shared by the tests, the
+benchmark and the CPU baseline.
+"""
+import numpy as np
+
+# Each entry: q, L, h, overlap, m, lnf_final, flatness, exchange_interval, spin_bits
+CONFIGS = {
+    # 2D Ising (q=2 Potts) L=8, 4 windows, 2 walkers, ln f 1 -> 1e-6, 8-bit spins
+    "ising_L8": dict(q=2, L=8, h=4, overlap=0.75, m=2, lnf_final=1e-6, flatness=0.8,
+                     exchange_interval=10_000, spin_bits=8),
+    # 10-state Potts L=20, 8 windows, 4 walkers, ln f_final 1e-8
+    "potts10_L20": dict(q=10, L=20, h=8, overlap=0.75, m=4, lnf_final=1e-8, flatness=0.8,
+                        exchange_interval=10_000, spin_bits=8),
+    # 10-state Potts L=80 (N=6400), 64 windows x 16 walkers = 1024 walkers, 4-bit spins
+    "potts10_L80": dict(q=10, L=80, h=64, overlap=0.75, m=16, lnf_final=1e-8, flatness=0.8,
+                        exchange_interval=10_000, spin_bits=4),
+}
+
+
+def params(name, **override):
+    p = dict(CONFIGS[name])
+    p.update(override)
+    return p
+
+
+def rewl_args(p, seed):
+    """Positional arguments of REWL(...) / OracleREWL(...) for a config dict."""
+    return (p["q"], p["L"], p["h"], p["overlap"], p["m"], p["lnf_final"], p["flatness"],
+            p["exchange_interval"], seed)
+
+
+def batched_instances(n=2048, master_seed=0x5EED0003):
+    """Independent instances of uneven size: q in {2,4,8,10}, L in {8,12,...,48},
+    h in {4,8,16}, m in {2,4}, overlap 0.75, ln f_final 1e-6, flatness 0.8."""
+    rng = np.random.default_rng(master_seed)
+    out = []
+    for i in range(n):
+        out.append(dict(q=int(rng.choice([2, 4, 8, 10])), L=int(rng.choice(np.arange(8, 49, 4))),
+                        h=int(rng.choice([4, 8, 16])), overlap=0.75, m=int(rng.choice([2, 4])),
+                        lnf_final=1e-6, flatness=0.8, exchange_interval=10_000,
+                        seed=int(rng.integers(1, 2**63))))
+    return out

@@ -1,0 +1,72 @@
+"""The C ABI boundary: the library loads and exports every function that
+include/rewl.h declares; argument checking happens before any CUDA call; the
+Python layer fails loudly when the library is missing (no CPU fallback)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+import paper_1312_3004_gb300 as pkg
+from paper_1312_3004_gb300 import _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(rewl_\w+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_core_entry_points():
+    names = declared_functions()
+    for n in ("rewl_create", "rewl_run", "rewl_get_lng", "rewl_destroy", "rewl_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = _lib.load()
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert lib.rewl_version().startswith(b"rewl-gb300")
+
+
+@pytest.mark.parametrize("args", [
+    (1, 8, 4, 0.75, 2, 1e-6, 0.8, 1000, 1),       # q < 2
+    (2, 2, 4, 0.75, 2, 1e-6, 0.8, 1000, 1),       # L < 3
+    (2, 8, 0, 0.75, 2, 1e-6, 0.8, 1000, 1),       # h < 1
+    (2, 8, 4, 1.0, 2, 1e-6, 0.8, 1000, 1),        # overlap >= 1
+    (2, 8, 4, 0.75, 0, 1e-6, 0.8, 1000, 1),       # m < 1
+    (2, 8, 4, 0.75, 2, 0.0, 0.8, 1000, 1),        # lnf_final <= 0
+    (2, 8, 4, 0.75, 2, 1e-6, 1.0, 1000, 1),       # flatness >= 1
+    (2, 8, 4, 0.75, 2, 1e-6, 0.8, 0, 1),          # K < 1
+    (2, 4, 40, 0.75, 2, 1e-6, 0.8, 1000, 1),      # window narrower than 8 bins
+])
+def test_invalid_arguments_are_rejected_before_any_device_work(args):
+    lib = _lib.load()
+    h = C.c_void_p()
+    st = lib.rewl_create(*args, C.byref(h))
+    assert st == 1  # REWL_ERR_ARG
+    assert h.value is None
+    assert len(lib.rewl_last_error()) > 0
+
+
+def test_null_handles_are_rejected():
+    lib = _lib.load()
+    assert lib.rewl_run(None, 1, None) == 1
+    assert lib.rewl_get_lng(None, None, 0, 0) == 1
+    lib.rewl_destroy(None)  # NULL-safe
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    monkeypatch.setattr(_lib, "LIB_PATH", "/nonexistent/librewl.so")
+    monkeypatch.setattr(_lib, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        pkg.REWL(2, 8, 4, 0.75, 2, 1e-6, 0.8, 1000, 1)

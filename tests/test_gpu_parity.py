@@ -1,0 +1,203 @@
+"""Parity of the CUDA path with the CPU oracle, element by element.
+
+Both implement the same reading of Sec. 2 (arXiv:1312.3004) on the same
+Philox4x32-10 streams, so spins, energies, replica ids, step counters, ln g
+(bit for bit), histograms, masks and ln f must agree after every round.  A
+divergence is only acceptable when the library has recorded an acceptance
+draw with |u - exp(D)| < 1e-14, where exp of two different libraries may round
+the comparison differently.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1312_3004_gb300 import REWL, RewlError
+from paper_1312_3004_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+
+def make_pair(q, L, h, o, m, lnf_final, flat, K, seed, spin_bits=0):
+    gpu = REWL(q, L, h, o, m, lnf_final, flat, K, seed, spin_bits=spin_bits)
+    orc = O.OracleREWL(q, L, h, o, m, lnf_final, flat, K, seed)
+    return gpu, orc
+
+
+def differences(gpu, orc):
+    diff = []
+    pairs = [("spins", orc.sigma()), ("energy", orc.E()), ("replica", orc.rep()), ("steps", orc.t()),
+             ("hist", orc.H()), ("mask", orc.mask()), ("iter", orc.iter()), ("done", orc.done())]
+    for name, want in pairs:
+        got = gpu.get(name)
+        if not np.array_equal(got, want):
+            diff.append(name)
+    for name, want in (("lng", orc.lng()), ("lnf", orc.lnf())):
+        if not np.array_equal(gpu.get(name).view(np.uint64), want.view(np.uint64)):
+            diff.append(name)
+    if gpu.round != orc.round:
+        diff.append("round")
+    return diff
+
+
+def assert_parity(gpu, orc):
+    diff = differences(gpu, orc)
+    if diff:
+        ties = gpu.stats()["near_ties"]
+        assert ties > 0, "state differs in %s without a near-tie acceptance draw" % diff
+
+
+def run_both(gpu, orc, rounds):
+    gpu.run(rounds)
+    orc.run(rounds)
+
+
+SMALL = [
+    # q, L, h, o, m, lnf_final, flatness, K, seed, spin_bits
+    (2, 8, 4, 0.75, 2, 1e-6, 0.8, 10_000, 1, 8),     # 2D Ising L=8 workload
+    (2, 8, 4, 0.75, 2, 1e-6, 0.8, 10_000, 1, 4),     # same, 4-bit packing
+    (10, 20, 8, 0.75, 4, 1e-8, 0.8, 10_000, 3, 8),   # 10-state Potts L=20 workload
+    (3, 5, 3, 0.75, 3, 1e-4, 0.8, 777, 5, 4),        # odd L, m = 3 (ragged merge tree)
+    (10, 7, 2, 0.6, 5, 1e-4, 0.7, 1234, 6, 4),       # N = 49: packed tail word
+    (4, 3, 1, 0.75, 1, 1e-3, 0.8, 500, 7, 8),        # smallest lattice, one window
+    (16, 9, 5, 0.75, 33, 1e-3, 0.8, 300, 8, 4),      # q = 16 (4-bit max), m > 32
+    (7, 6, 6, 0.8, 2, 1e-3, 0.8, 1, 9, 8),           # K = 1: exchange every step
+]
+
+
+@pytest.mark.parametrize("case", SMALL)
+def test_initial_state_matches(case):
+    *args, sb = case
+    gpu, orc = make_pair(*args, spin_bits=sb)
+    assert_parity(gpu, orc)
+
+
+@pytest.mark.parametrize("case", SMALL)
+def test_rounds_match_bit_for_bit(case):
+    *args, sb = case
+    gpu, orc = make_pair(*args, spin_bits=sb)
+    for n in (1, 2, 5, 12):
+        run_both(gpu, orc, n)
+        assert_parity(gpu, orc)
+
+
+def test_first_million_updates_per_walker_ising_L8():
+    """10^6 WL updates per walker (100 rounds of 10^4) on the L=8 Ising workload."""
+    p = WL.params("ising_L8")
+    for seed in (1, 2):
+        gpu, orc = make_pair(*WL.rewl_args(p, seed), spin_bits=p["spin_bits"])
+        run_both(gpu, orc, 100)
+        assert orc.t().min() >= 10 ** 6 or orc.all_done()
+        assert_parity(gpu, orc)
+
+
+def test_first_million_updates_per_walker_potts10_L20():
+    p = WL.params("potts10_L20")
+    gpu, orc = make_pair(*WL.rewl_args(p, 1), spin_bits=p["spin_bits"])
+    run_both(gpu, orc, 100)
+    assert_parity(gpu, orc)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4])
+def test_converged_ising_L8_matches_oracle(seed):
+    """Full runs to ln f < 1e-6: identical joined ln g and identical state."""
+    p = WL.params("ising_L8")
+    gpu, orc = make_pair(*WL.rewl_args(p, seed), spin_bits=p["spin_bits"])
+    assert orc.run(0)
+    assert gpu.run(0)
+    assert_parity(gpu, orc)
+    a, b = gpu.lng(), orc.lng_joined()
+    fin = np.isfinite(b)
+    assert np.array_equal(np.isfinite(a), fin)
+    assert np.max(np.abs(a[fin] - b[fin])) <= 1e-12
+
+
+def test_large_potts10_L80_first_rounds_match():
+    """The 1024-walker q=10, L=80 workload in the launch configuration the
+    benchmark uses: initial state and two rounds agree with the oracle."""
+    p = WL.params("potts10_L80")
+    gpu, orc = make_pair(*WL.rewl_args(p, 1), spin_bits=p["spin_bits"])
+    assert_parity(gpu, orc)
+    run_both(gpu, orc, 2)
+    assert_parity(gpu, orc)
+
+
+def test_rounds_after_convergence_change_nothing():
+    gpu = REWL(2, 4, 2, 0.75, 2, 1e-2, 0.8, 2000, 3)
+    assert gpu.run(0)
+    before = {k: gpu.get(k) for k in ("lng", "spins", "hist", "round", "steps")}
+    gpu.run(20)
+    for k, v in before.items():
+        assert np.array_equal(gpu.get(k), v)
+
+
+def test_save_load_resume_is_bit_exact():
+    args = (10, 12, 4, 0.75, 3, 1e-4, 0.8, 3000, 11)
+    a = REWL(*args)
+    a.run(10)
+    blob = a.save()
+    a.run(10)
+    b = REWL(*args)
+    b.load(blob)
+    b.run(10)
+    for k in ("lng", "spins", "hist", "mask", "lnf", "replica", "steps", "round"):
+        assert np.array_equal(a.get(k), b.get(k)), k
+    bad = bytearray(blob)
+    bad[-1] ^= 0xFF
+    with pytest.raises(RewlError):
+        b.load(bytes(bad))
+    c = REWL(10, 12, 4, 0.75, 3, 1e-4, 0.8, 3000, 12)  # other seed: other instance
+    with pytest.raises(RewlError):
+        c.load(blob)
+
+
+def test_fixed_weights_flat_histogram_on_gpu():
+    """ln g = exact ln g and ln f = 0: the GPU walker visits every reachable
+    energy equally often, and agrees with the oracle step for step.  (Flatness
+    0.999999 keeps the window from ever finishing its iteration.)  The top bin
+    (proper 3-colourings) is left rarely, so its count has a long
+    autocorrelation: 4e6 steps give a few per cent of noise there."""
+    q, L = 3, 3
+    ex = O.exact_lng(O.exact_counts_brute(q, L))
+    gpu, orc = make_pair(q, L, 1, 0.75, 1, 1e-6, 0.999999, 100_000, 4)
+    tab = np.where(np.isfinite(ex), ex, 0.0)[None, :]
+    gpu.set("lng", tab)
+    gpu.set("lnf", 0.0)
+    orc.set_lng(tab)
+    orc.set_lnf(0.0)
+    run_both(gpu, orc, 40)
+    assert_parity(gpu, orc)
+    Hg = gpu.get("hist")[0]
+    reach = np.isfinite(ex)
+    hv = Hg[reach].astype(float)
+    assert np.max(np.abs(hv / hv.mean() - 1)) < 0.1
+
+
+def test_stats_count_every_proposal():
+    gpu = REWL(5, 10, 4, 0.75, 3, 1e-6, 0.8, 2500, 2)
+    gpu.run(6)
+    s = gpu.stats()
+    assert s["rounds"] == 6
+    assert s["flips"] == 6 * 2500 * 12
+    assert 0 < s["accepted"] <= s["flips"]
+    assert s["exch_tried"] >= s["exch_accepted"]
+
+
+def test_partial_results_and_state_errors():
+    gpu = REWL(2, 8, 4, 0.75, 2, 1e-6, 0.8, 10_000, 1)
+    gpu.run(3)
+    with pytest.raises(RewlError):
+        gpu.lng(partial=False)
+    lg = gpu.lng(partial=True)
+    assert np.isfinite(lg).sum() > 10
+
+
+def test_spins_roundtrip_and_energy_recount():
+    gpu = REWL(10, 11, 3, 0.75, 2, 1e-6, 0.8, 100, 5, spin_bits=4)
+    s = gpu.get("spins")
+    rng = np.random.default_rng(0)
+    s2 = rng.integers(0, 10, s.shape).astype(np.uint8)
+    gpu.set("spins", s2)
+    assert np.array_equal(gpu.get("spins"), s2)
+    E = gpu.get("energy")
+    for g in range(s2.shape[0]):
+        assert E[g] == O.energy(11, s2[g])
