@@ -197,6 +197,37 @@ rewl_status rewl_set_field(rewl_t h, int field, const void *in, size_t bytes);
 rewl_status rewl_save(rewl_t h, void *buf, size_t *len);
 rewl_status rewl_load(rewl_t h, const void *buf, size_t len);
 
+/* A whole run without allocating: for callers that cannot call cudaMalloc,
+ * e.g. code under a framework whose caching allocator owns the device memory,
+ * a process with a fixed device-memory budget, or a latency-critical loop that
+ * cannot take the device-wide synchronisation of cudaMalloc / cudaFree.
+ * (The paper has no counterpart: this is a deployment variant of
+ * rewl_create + rewl_run.)
+ *
+ * Runs the instance described by `params` (spin_bits as in rewl_create_ext)
+ * for up to max_rounds exchange rounds (<= 0: until converged) with all of its
+ * working state in one fixed device array of 16 MiB that the library reserves
+ * on every GPU that loads it, for the life of the process.  Calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ * Outputs (caller-owned DEVICE memory on the current device):
+ *   lng_out  h * (W + 1) doubles: ln g of walker 0 of every window, window-major
+ *            (the rows rewl_get_field(REWL_FIELD_LNG) holds for walkers i*m);
+ *   mask_out h * (W + 1) bytes: visited-bin masks, or NULL;
+ *   out_bins must equal h * (W + 1).
+ * *converged (host, may be NULL) is 1 when every window finished.  Work is
+ * queued on `stream` (cudaStream_t as void*, NULL = default stream) and the
+ * call synchronises it before returning.
+ * The first call on a device looks up the array's device address (with that
+ * device current) and caches it; make that first call before any stream
+ * capture.  The array is shared by every call: each call clears what must
+ * start at zero, and calls whose work overlaps on the GPU race on it.
+ * Errors: REWL_ERR_ARG (parameters, NULL lng_out, wrong out_bins, or an
+ * instance whose state exceeds the 16 MiB array), REWL_ERR_CUDA,
+ * REWL_ERR_OVERFLOW, REWL_ERR_STATE (window entry failed). */
+rewl_status rewl_run_static(const rewl_params *params, int spin_bits, long long max_rounds,
+                            double *lng_out, unsigned char *mask_out, size_t out_bins,
+                            int *converged, void *stream);
+
 /* Release the handle and its device memory.  NULL is ignored. */
 void rewl_destroy(rewl_t h);
 

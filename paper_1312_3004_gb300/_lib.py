@@ -76,6 +76,8 @@ def load():
                  "rewl_sync", "rewl_run_phase", "rewl_get_lng", "rewl_get_window_lng", "rewl_get_info",
                  "rewl_get_stats", "rewl_get_field", "rewl_set_field", "rewl_save", "rewl_load"):
         getattr(L, name).restype = st
+    L.rewl_run_static.argtypes = [C.POINTER(Params), i32, ll, vp, vp, sz, C.POINTER(C.c_int), vp]
+    L.rewl_run_static.restype = st
     L.rewl_destroy.argtypes = [H]
     L.rewl_destroy.restype = None
     L.rewl_last_error.argtypes = []

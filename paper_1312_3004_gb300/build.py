@@ -1,6 +1,6 @@
 """Build the CUDA library librewl.so (sm_103a) in-tree.
 
-Two translation units are compiled in parallel with nvcc and linked into
+The translation units are compiled in parallel with nvcc and linked into
 paper_1312_3004_gb300/_build/librewl.so.  No CPU code path is built: the
 library is the GPU implementation only.
 """
@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "librewl.so")
-SOURCES = ["rewl_kernels.cu", "rewl_host.cu"]
+SOURCES = ["rewl_kernels.cu", "rewl_host.cu", "rewl_static.cu"]
 HEADERS = ["rewl_internal.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

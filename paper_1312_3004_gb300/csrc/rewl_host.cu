@@ -62,6 +62,8 @@ bool window_geometry(int L, int h, double o, std::vector<int32_t> &e_lo, int &W)
 
 }  // namespace
 
+void rewl::set_error(const char *msg) { g_last_error = msg; }
+
 struct rewl_s {
     rewl_params prm{};
     Model M{};

@@ -77,4 +77,7 @@ cudaError_t launch_set_spins(const Model &M, const State &S, const uint8_t *spin
 cudaError_t launch_get_spins(const Model &M, const State &S, uint8_t *spins_dev, cudaStream_t s);
 size_t sweep_smem_per_walker(const Model &M);
 
+// Record the message returned by rewl_last_error() on this thread (rewl_host.cu).
+void set_error(const char *msg);
+
 }  // namespace rewl
