@@ -290,6 +290,10 @@ def run_ours(args):
         "e2e": {"value": e2e_val, "unit": "flips/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 64,
                 "call": "rewl_run(handle, 1 round) incl. status read-back", "steps": e2e_steps},
         "gpu_launches": 3 * args.steps,
+        "sweep_plan": {"kernel": "fast" if r.get_option(_lib.OPT_SWEEP_KERNEL) == 0 else "reference",
+                       "lanes_per_walker": r.get_option(_lib.OPT_LANES),
+                       "walkers_per_cta": r.get_option(_lib.OPT_WALKERS_PER_CTA)},
+        "slow_path_decisions": r.stats()["slow_decisions"],
         "clocks": clocks,
         "wall_s_timed": wall,
         "sweep_share": sum(sweep_ms) / total_ms,

@@ -86,6 +86,7 @@ typedef struct rewl_stats {
     long long exch_tried;      /* exchange pairs evaluated with Eq. 1          */
     long long exch_accepted;   /* exchanges carried out                        */
     long long near_ties;       /* acceptance draws with |u - exp(D)| < 1e-14   */
+    long long slow_decisions;  /* WL decisions the fast sweep took in binary64 */
     int windows_done;          /* windows that reached ln f_final              */
     int converged;             /* 1 when every window is done                  */
     double min_lnf;            /* smallest ln f over windows                   */
@@ -138,6 +139,20 @@ rewl_status rewl_run_async(rewl_t h, long long rounds);
  * REWL_ERR_CUDA (launch failure). */
 enum { REWL_PHASE_SWEEP = 0, REWL_PHASE_CHECK = 1, REWL_PHASE_EXCHANGE = 2 };
 rewl_status rewl_run_phase(rewl_t h, int phase);
+
+/* Tuning options of a handle (no effect on results: every choice computes
+ * the same states bit for bit):
+ *   REWL_OPT_SWEEP_KERNEL  0 = fast sweep (integer acceptance path with a
+ *                          binary64 fallback), 1 = binary64 reference sweep
+ *   REWL_OPT_LANES         lanes per walker of the fast sweep: 0 = chosen from
+ *                          the walker count, or 1, 2, 4, 8, 16, 32
+ *   REWL_OPT_WALKERS_PER_CTA  (read-only) walkers per CTA of the current plan
+ * rewl_set_option synchronises the stream and re-plans the sweep.
+ * Errors: REWL_ERR_ARG (unknown option or value, or a plan that does not fit
+ * in shared memory). */
+enum { REWL_OPT_SWEEP_KERNEL = 0, REWL_OPT_LANES = 1, REWL_OPT_WALKERS_PER_CTA = 2 };
+rewl_status rewl_set_option(rewl_t h, int option, long long value);
+rewl_status rewl_get_option(rewl_t h, int option, long long *value);
 
 /* Synchronise the handle's stream and report its device status:
  * *converged (may be NULL) as in rewl_run. */

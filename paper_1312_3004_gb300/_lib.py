@@ -16,6 +16,7 @@ STATUS_NAMES = {0: "REWL_OK", 1: "REWL_ERR_ARG", 2: "REWL_ERR_NOMEM", 3: "REWL_E
 
 FIELD_SPINS, FIELD_ENERGY, FIELD_REPLICA, FIELD_STEPS, FIELD_LNG, FIELD_HIST = 0, 1, 2, 3, 4, 5
 PHASE_SWEEP, PHASE_CHECK, PHASE_EXCHANGE = 0, 1, 2
+OPT_SWEEP_KERNEL, OPT_LANES, OPT_WALKERS_PER_CTA = 0, 1, 2
 FIELD_MASK, FIELD_LNF, FIELD_ITER, FIELD_DONE, FIELD_ELO, FIELD_ROUND = 6, 7, 8, 9, 10, 11
 
 
@@ -39,7 +40,7 @@ class Info(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("rounds", C.c_longlong), ("flips", C.c_longlong), ("accepted", C.c_longlong),
                 ("exch_tried", C.c_longlong), ("exch_accepted", C.c_longlong),
-                ("near_ties", C.c_longlong), ("windows_done", C.c_int), ("converged", C.c_int),
+                ("near_ties", C.c_longlong), ("slow_decisions", C.c_longlong), ("windows_done", C.c_int), ("converged", C.c_int),
                 ("min_lnf", C.c_double), ("max_lnf", C.c_double)]
 
 
@@ -64,6 +65,8 @@ def load():
     L.rewl_run_async.argtypes = [H, ll]
     L.rewl_sync.argtypes = [H, C.POINTER(C.c_int)]
     L.rewl_run_phase.argtypes = [H, i32]
+    L.rewl_set_option.argtypes = [H, i32, ll]
+    L.rewl_get_option.argtypes = [H, i32, C.POINTER(C.c_longlong)]
     L.rewl_get_lng.argtypes = [H, vp, sz, i32]
     L.rewl_get_window_lng.argtypes = [H, i32, vp, sz, C.POINTER(C.c_int)]
     L.rewl_get_info.argtypes = [H, C.POINTER(Info)]
@@ -73,7 +76,7 @@ def load():
     L.rewl_save.argtypes = [H, vp, C.POINTER(sz)]
     L.rewl_load.argtypes = [H, vp, sz]
     for name in ("rewl_create", "rewl_create_ext", "rewl_set_stream", "rewl_run", "rewl_run_async",
-                 "rewl_sync", "rewl_run_phase", "rewl_get_lng", "rewl_get_window_lng", "rewl_get_info",
+                 "rewl_sync", "rewl_run_phase", "rewl_set_option", "rewl_get_option", "rewl_get_lng", "rewl_get_window_lng", "rewl_get_info",
                  "rewl_get_stats", "rewl_get_field", "rewl_set_field", "rewl_save", "rewl_load"):
         getattr(L, name).restype = st
     L.rewl_run_static.argtypes = [C.POINTER(Params), i32, ll, vp, vp, sz, C.POINTER(C.c_int), vp]

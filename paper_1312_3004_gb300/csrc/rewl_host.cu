@@ -77,6 +77,7 @@ struct rewl_s {
     Ctl *h_ctl = nullptr;  // pinned mirror of the device control block
     std::vector<int32_t> e_lo;
     cudaGraphExec_t graph = nullptr;
+    int sms = 0, smem_optin = 0;
     // byte offsets of the state arrays inside dmem (for save / load)
     struct Part { size_t off, bytes; };
     std::vector<Part> parts;
@@ -280,10 +281,12 @@ rewl_status rewl_create_ext(const rewl_params *prm, int spin_bits, rewl_t *out) 
     int sms = 0, optin = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
-    if (rewl::sweep_smem_per_walker(M) > (size_t)optin)
-        return cleanup(fail(REWL_ERR_ARG, "one walker needs %zu bytes of shared memory (> %d)",
-                            rewl::sweep_smem_per_walker(M), optin));
+    h->sms = sms;
+    h->smem_optin = optin;
     h->plan = rewl::plan_sweep(M, sms, (size_t)optin);
+    if (h->plan.P < 1)
+        return cleanup(fail(REWL_ERR_ARG, "one walker needs %zu bytes of shared memory (> %d)",
+                            rewl::fast_smem_per_walker(M, h->plan.lanes), optin));
 
     // one allocation, carved into 256-byte aligned arrays
     const size_t G = (size_t)M.G, B = (size_t)M.B, hh = (size_t)M.h;
@@ -383,6 +386,41 @@ rewl_status rewl_run_phase(rewl_t h, int phase) {
     return REWL_OK;
 }
 
+rewl_status rewl_set_option(rewl_t h, int option, long long value) {
+    if (!h) return fail(REWL_ERR_ARG, "NULL handle");
+    int kind = h->plan.kind, lanes = h->plan.lanes;
+    if (option == REWL_OPT_SWEEP_KERNEL) {
+        if (value != 0 && value != 1) return fail(REWL_ERR_ARG, "sweep kernel %lld not 0 or 1", value);
+        kind = value == 0 ? rewl::SWEEP_FAST : rewl::SWEEP_REFERENCE;
+        lanes = 0;
+    } else if (option == REWL_OPT_LANES) {
+        if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8 && value != 16 && value != 32)
+            return fail(REWL_ERR_ARG, "lanes per walker %lld not 0, 1, 2, 4, 8, 16 or 32", value);
+        lanes = (int)value;
+    } else {
+        return fail(REWL_ERR_ARG, "unknown option %d", option);
+    }
+    const rewl::SweepPlan plan = rewl::plan_sweep(h->M, h->sms, (size_t)h->smem_optin, kind, lanes);
+    if (plan.P < 1) return fail(REWL_ERR_ARG, "configuration does not fit in shared memory");
+    REWL_CUDA(cudaStreamSynchronize(h->stream));
+    REWL_CUDA(rewl::prepare_sweep(h->M, plan));
+    h->plan = plan;
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    return build_graph(h);
+}
+
+rewl_status rewl_get_option(rewl_t h, int option, long long *value) {
+    if (!h || !value) return fail(REWL_ERR_ARG, "NULL argument");
+    if (option == REWL_OPT_SWEEP_KERNEL) *value = h->plan.kind == rewl::SWEEP_FAST ? 0 : 1;
+    else if (option == REWL_OPT_LANES) *value = h->plan.lanes;
+    else if (option == REWL_OPT_WALKERS_PER_CTA) *value = h->plan.P;
+    else return fail(REWL_ERR_ARG, "unknown option %d", option);
+    return REWL_OK;
+}
+
 rewl_status rewl_sync(rewl_t h, int *converged) {
     if (!h) return fail(REWL_ERR_ARG, "NULL handle");
     rewl_status st = read_ctl(h);
@@ -458,6 +496,7 @@ rewl_status rewl_get_stats(rewl_t h, rewl_stats *s) {
     s->exch_tried = (long long)c.xtried;
     s->exch_accepted = (long long)c.xacc;
     s->near_ties = (long long)c.ties;
+    s->slow_decisions = (long long)c.slow;
     s->windows_done = 0;
     s->min_lnf = INFINITY;
     s->max_lnf = -INFINITY;

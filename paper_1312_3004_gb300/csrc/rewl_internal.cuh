@@ -59,7 +59,11 @@ struct State {
     Ctl *ctl;             // control block
 };
 
+enum : int { SWEEP_REFERENCE = 0, SWEEP_FAST = 1 };
+
 struct SweepPlan {
+    int kind;        // SWEEP_REFERENCE (binary64 on the chain) or SWEEP_FAST
+    int lanes;       // lanes per walker of the fast sweep (1, 2, 4, 8, 16, 32)
     int P;           // walkers per CTA
     int threads;     // CTA size
     int grid;        // CTAs
@@ -68,7 +72,9 @@ struct SweepPlan {
 
 // Launchers (rewl_kernels.cu).  All enqueue on `s` and return the launch error.
 cudaError_t launch_init(const Model &M, const State &S, cudaStream_t s);
-SweepPlan plan_sweep(const Model &M, int num_sms, size_t smem_optin);
+// kind: SWEEP_REFERENCE / SWEEP_FAST; lanes: 0 = choose from the walker count.
+// A plan with P == 0 means the configuration does not fit (shared memory).
+SweepPlan plan_sweep(const Model &M, int num_sms, size_t smem_optin, int kind = SWEEP_FAST, int lanes = 0);
 cudaError_t prepare_sweep(const Model &M, const SweepPlan &p);
 cudaError_t launch_sweep(const Model &M, const State &S, const SweepPlan &p, cudaStream_t s);
 cudaError_t launch_window_check(const Model &M, const State &S, cudaStream_t s);
@@ -76,6 +82,8 @@ cudaError_t launch_exchange(const Model &M, const State &S, cudaStream_t s);
 cudaError_t launch_set_spins(const Model &M, const State &S, const uint8_t *spins_dev, cudaStream_t s);
 cudaError_t launch_get_spins(const Model &M, const State &S, uint8_t *spins_dev, cudaStream_t s);
 size_t sweep_smem_per_walker(const Model &M);
+size_t fast_smem_per_walker(const Model &M, int lanes);
+cudaError_t launch_sweep_fast(const Model &M, const State &S, const SweepPlan &p, cudaStream_t s, bool prepare);
 
 // Record the message returned by rewl_last_error() on this thread (rewl_host.cu).
 void set_error(const char *msg);

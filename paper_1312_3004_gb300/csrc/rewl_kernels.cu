@@ -435,8 +435,25 @@ size_t sweep_smem_per_walker(const Model &M) {
     return (size_t)M.B * (sizeof(double) + sizeof(uint32_t)) + (size_t)M.wpc * sizeof(uint32_t);
 }
 
-SweepPlan plan_sweep(const Model &M, int num_sms, size_t smem_optin) {
+SweepPlan plan_sweep(const Model &M, int num_sms, size_t smem_optin, int kind, int lanes) {
     SweepPlan p{};
+    p.kind = kind;
+    if (kind == SWEEP_FAST) {
+        if (lanes <= 0) lanes = M.G <= 16 * num_sms ? 32 : (M.G <= 64 * num_sms ? 8 : 1);
+        p.lanes = lanes;
+        const size_t per = fast_smem_per_walker(M, lanes);
+        int cap = (int)(smem_optin / per);
+        if (cap > 256 / lanes) cap = 256 / lanes;
+        int P = (M.G + num_sms - 1) / num_sms;
+        if (P < 1) P = 1;
+        if (P > cap) P = cap;
+        p.P = P;
+        p.threads = ((P * lanes + 31) / 32) * 32;
+        p.grid = P > 0 ? (M.G + P - 1) / P : 0;
+        p.smem = per * (size_t)P;
+        return p;
+    }
+    p.lanes = 1;
     const size_t per = sweep_smem_per_walker(M);
     int cap = (int)(smem_optin / per);
     if (cap > 256) cap = 256;
@@ -446,7 +463,7 @@ SweepPlan plan_sweep(const Model &M, int num_sms, size_t smem_optin) {
     p.P = P;
     p.threads = ((P + 31) / 32) * 32;
     if (p.threads < 128) p.threads = 128;
-    p.grid = (M.G + P - 1) / P;
+    p.grid = P > 0 ? (M.G + P - 1) / P : 0;
     p.smem = per * (size_t)P;
     return p;
 }
@@ -459,12 +476,14 @@ cudaError_t launch_init(const Model &M, const State &S, cudaStream_t s) {
 }
 
 cudaError_t prepare_sweep(const Model &M, const SweepPlan &p) {
+    if (p.kind == SWEEP_FAST) return launch_sweep_fast(M, State{}, p, nullptr, true);
     if (M.bits == 8)
         return cudaFuncSetAttribute(sweep_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
     return cudaFuncSetAttribute(sweep_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
 }
 
 cudaError_t launch_sweep(const Model &M, const State &S, const SweepPlan &p, cudaStream_t s) {
+    if (p.kind == SWEEP_FAST) return launch_sweep_fast(M, S, p, s, false);
     if (M.bits == 8) sweep_kernel<8><<<p.grid, p.threads, p.smem, s>>>(M, S, p.P);
     else sweep_kernel<4><<<p.grid, p.threads, p.smem, s>>>(M, S, p.P);
     return cudaGetLastError();

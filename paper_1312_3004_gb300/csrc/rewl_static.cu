@@ -130,7 +130,6 @@ extern "C" rewl_status rewl_run_static(const rewl_params *prm, int spin_bits, lo
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (rewl::sweep_smem_per_walker(M) > (size_t)optin) return fail_static(REWL_ERR_ARG, "lattice too large");
 
     rewl::State S{};
     S.spins = (uint32_t *)(base + offs[0]);
@@ -148,6 +147,7 @@ extern "C" rewl_status rewl_run_static(const rewl_params *prm, int spin_bits, lo
 
     cudaStream_t s = (cudaStream_t)stream;
     const rewl::SweepPlan plan = rewl::plan_sweep(M, sms, (size_t)optin);
+    if (plan.P < 1) return fail_static(REWL_ERR_ARG, "lattice too large for shared memory");
     rewl::Ctl ctl{};
     auto read_ctl = [&]() -> rewl_status {
         cudaError_t e2 = cudaMemcpyAsync(&ctl, S.ctl, sizeof ctl, cudaMemcpyDeviceToHost, s);

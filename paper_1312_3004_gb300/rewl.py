@@ -78,6 +78,14 @@ class REWL:
         """Queue one phase (_lib.PHASE_SWEEP / PHASE_CHECK / PHASE_EXCHANGE)."""
         check(self._L.rewl_run_phase(self._h, phase))
 
+    def set_option(self, option, value):
+        check(self._L.rewl_set_option(self._h, option, value))
+
+    def get_option(self, option):
+        v = C.c_longlong(0)
+        check(self._L.rewl_get_option(self._h, option, C.byref(v)))
+        return v.value
+
     def sync(self):
         conv = C.c_int(0)
         check(self._L.rewl_sync(self._h, C.byref(conv)))

@@ -80,6 +80,27 @@ def test_rounds_match_bit_for_bit(case):
         assert_parity(gpu, orc)
 
 
+SWEEPS = [("reference", 1, 0), ("lanes1", 0, 1), ("lanes2", 0, 2), ("lanes4", 0, 4), ("lanes8", 0, 8),
+          ("lanes16", 0, 16), ("lanes32", 0, 32)]
+
+
+@pytest.mark.parametrize("sweep", SWEEPS, ids=[s[0] for s in SWEEPS])
+@pytest.mark.parametrize("case", [SMALL[0], SMALL[2], SMALL[3], SMALL[4], SMALL[6]])
+def test_every_sweep_variant_matches(case, sweep):
+    """The binary64 reference sweep and the fast sweep at every lane-group
+    width produce the oracle's states bit for bit."""
+    from paper_1312_3004_gb300 import _lib
+    *args, sb = case
+    gpu, orc = make_pair(*args, spin_bits=sb)
+    _, kind, lanes = sweep
+    gpu.set_option(_lib.OPT_SWEEP_KERNEL, kind)
+    if kind == 0:
+        gpu.set_option(_lib.OPT_LANES, lanes)
+    for n in (1, 4, 10):
+        run_both(gpu, orc, n)
+        assert_parity(gpu, orc)
+
+
 def test_first_million_updates_per_walker_ising_L8():
     """10^6 WL updates per walker (100 rounds of 10^4) on the L=8 Ising workload."""
     p = WL.params("ising_L8")
