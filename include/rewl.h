@@ -87,6 +87,7 @@ typedef struct rewl_stats {
     long long exch_accepted;   /* exchanges carried out                        */
     long long near_ties;       /* acceptance draws with |u - exp(D)| < 1e-14   */
     long long slow_decisions;  /* WL decisions the fast sweep took in binary64 */
+    long long seq_steps;       /* WL steps the fast sweep resolved one at a time */
     int windows_done;          /* windows that reached ln f_final              */
     int converged;             /* 1 when every window is done                  */
     double min_lnf;            /* smallest ln f over windows                   */

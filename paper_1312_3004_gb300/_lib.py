@@ -40,7 +40,8 @@ class Info(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("rounds", C.c_longlong), ("flips", C.c_longlong), ("accepted", C.c_longlong),
                 ("exch_tried", C.c_longlong), ("exch_accepted", C.c_longlong),
-                ("near_ties", C.c_longlong), ("slow_decisions", C.c_longlong), ("windows_done", C.c_int), ("converged", C.c_int),
+                ("near_ties", C.c_longlong), ("slow_decisions", C.c_longlong),
+                ("seq_steps", C.c_longlong), ("windows_done", C.c_int), ("converged", C.c_int),
                 ("min_lnf", C.c_double), ("max_lnf", C.c_double)]
 
 

@@ -497,6 +497,7 @@ rewl_status rewl_get_stats(rewl_t h, rewl_stats *s) {
     s->exch_accepted = (long long)c.xacc;
     s->near_ties = (long long)c.ties;
     s->slow_decisions = (long long)c.slow;
+    s->seq_steps = (long long)c.seq;
     s->windows_done = 0;
     s->min_lnf = INFINITY;
     s->max_lnf = -INFINITY;

@@ -23,6 +23,7 @@ struct Ctl {
     unsigned long long xacc;      // exchanges carried out
     unsigned long long ties;      // |u - exp(D)| < 1e-14 acceptance draws
     unsigned long long slow;      // WL decisions resolved on the FP64 path
+    unsigned long long seq;       // WL steps the fast sweep resolved one at a time
 };
 
 enum : unsigned int {

@@ -1,28 +1,29 @@
 // rewl_sweep.cu -- the fast WL sweep (Sec. 2 of arXiv:1312.3004) for sm_103a.
 //
-// Same arithmetic as the binary64 reference sweep in rewl_kernels.cu, bit for
+// Same states as the binary64 reference sweep in rewl_kernels.cu, bit for
 // bit, organised for a GPU whose FP64 pipe is narrow and slow (GB300: one DADD
 // has ~64 cycles of latency and ~2 per clock per SM of throughput):
 //
 //  * A group of S lanes (S = 1 .. 32, a power of two) owns one walker.  Each
 //    lane prepares one of the next S proposals in parallel: Philox block,
 //    site, new value, energy change against the lattice at the start of the
-//    batch, and two integer acceptance thresholds.  The group then resolves the
-//    S proposals in order; a proposal whose neighbourhood an earlier accepted
+//    batch, and an integer acceptance bracket.  The group then resolves the S
+//    proposals in order; a proposal whose neighbourhood an earlier accepted
 //    flip of the same batch touched is recomputed from the current lattice.
-//  * ln g values are non-negative binary64 numbers, so their bit patterns
-//    compare like the values.  D = bits(ln g(E')) - bits(ln g(E)) is the exact
-//    difference in units of the last place when both lie in the same binade,
-//    and "u < exp(ln g(E) - ln g(E'))" becomes D < T with T = -ln(u) / ulp.  T is
-//    bracketed by [t_lo, t_hi) from a float estimate of -ln u with a proven
-//    error margin; D < t_lo accepts and D >= t_hi rejects with certainty.  Only a
-//    D inside the bracket (or operands in different binades) takes the
-//    binary64 path exp(a - b) -- the same operation the reference performs.
-//  * ln g(E) += ln f is an integer add of ln f / ulp to the bit pattern while
-//    the sum stays in the binade (ln f = 2^-k is an exact multiple of the ulp);
-//    otherwise a binary64 add.
-//  * The current bin's ln g and visit count live in registers and are written
-//    to shared memory when the walker leaves the bin.
+//  * Fixed-point shadow of ln g: for the launch, every ln g value v of the
+//    walker is also held as F(v) = floor(v / u) with u = 2^(e_w - 1075), where
+//    e_w is nine binades below the largest value the launch can reach (so F
+//    fits in 63 bits with a binade of headroom, and |F(v) u - v| < u).  D = F(ln g(E')) - F(ln g(E)) is
+//    then within one unit of (ln g(E') - ln g(E)) / u, and the reference test
+//    "u_rnd < exp(ln g(E) - ln g(E'))" is decided by D < T_lo (accept) or
+//    D >= T_hi (reject), with [T_lo, T_hi) bracketing -ln(u_rnd) / u with a
+//    proven margin.  Only D inside the bracket (about 1e-5 of the decisions)
+//    takes the binary64 path exp(a - b) -- the operation the reference does.
+//  * ln g(E) += ln f is an integer add on the binary64 bit pattern while the
+//    sum stays in the binade (ln f = 2^-k is then an exact multiple of the
+//    ulp), and F += ln f / u; otherwise a binary64 add and F is recomputed.
+//  * The current bin's ln g, its shadow and its visit count live in registers
+//    and are written to shared memory when the walker leaves the bin.
 #include <cstdint>
 
 #include "rewl_internal.cuh"
@@ -85,31 +86,38 @@ __device__ __forceinline__ unsigned long long u53(uint32_t hi, uint32_t lo) {
     return ((unsigned long long)(hi >> 5) << 26) | (lo >> 6);
 }
 
-constexpr long long kNoReject = 0x7fffffffffffffffLL;
+// Upper bracket end that never rejects inside a window (in-window |D| < 2^62).
+constexpr long long kNoReject = 1LL << 62;
+// Shadow value of the four bins beyond each end of a window: every proposal
+// there has D >= 2^62 >= t_hi and is rejected like an out-of-window move.
+constexpr long long kOutside = 0x7fffffffffffffffLL;
+constexpr int kPad = 4;
+constexpr long long kMant = (1LL << 52) - 1, kHidden = 1LL << 52;
 
-// floor / ceil of x * 2^k as a 64-bit integer, saturating at 2^62 (x >= 0).
+// floor / ceil of x * 2^k as a 64-bit integer, saturating at 2^61 (x >= 0).
 __device__ __forceinline__ long long scaled_floor(float x, int k) {
     if (x <= 0.0f) return 0;
-    if (k > 120) return 1LL << 62;
+    if (k > 120) return 1LL << 61;
     const float y = x * __int_as_float((k + 127) << 23);
-    return y >= 0x1p62f ? (1LL << 62) : __float2ll_rd(y);
+    return y >= 0x1p61f ? (1LL << 61) : __float2ll_rd(y);
 }
 __device__ __forceinline__ long long scaled_ceil(float x, int k) {
     if (x <= 0.0f) return 0;
-    if (k > 120) return 1LL << 62;
+    if (k > 120) return 1LL << 61;
     const float y = x * __int_as_float((k + 127) << 23);
-    return y >= 0x1p62f ? (1LL << 62) : __float2ll_ru(y);
+    return y >= 0x1p61f ? (1LL << 61) : __float2ll_ru(y);
 }
 
-// Bracket of T = -ln(u) / ulp(binade e0): accept-certain if D < t_lo,
-// reject-certain if D >= t_hi.  uf = u with relative error <= 2^-23 (24 + 24
-// bits, one rounding; top >= 1 makes the 5 dropped bits <= 2^-24 relative);
-// logf is within 1 ulp; so |Lf - (-ln u)| <= (Lf + 1) 2^-22.9 and the margin
-// (Lf + 1) 2^-18 leaves a factor > 8.  exp's own error (1 ulp of binary64)
-// and the rounding of Lf -/+ margin are far inside that slack.
-__device__ __forceinline__ void accept_bracket(unsigned long long U, int e0, long long &t_lo, long long &t_hi) {
+// Bracket of T = -ln(u) / unit, unit = 2^-k: accept for sure if D < t_lo,
+// reject for sure if D >= t_hi, where D is within one unit of the true
+// difference.  uf = u with relative error <= 2^-23 (24 + 24 bits, one
+// rounding; top >= 1 makes the 5 dropped bits <= 2^-24 relative); logf is
+// within 1 ulp; so |Lf - (-ln u)| <= (Lf + 1) 2^-22.9, and the margin
+// (Lf + 1) 2^-18 leaves a factor > 8 for that, for exp's own error (1 ulp of
+// binary64) and for the rounding of Lf -/+ margin.
+__device__ __forceinline__ void accept_bracket(unsigned long long U, int k, long long &t_lo, long long &t_hi) {
     const uint32_t top = (uint32_t)(U >> 29);
-    if (top == 0u || e0 == 0) {  // u < 2^-24, or no binade yet: decide exactly
+    if (top == 0u) {  // u < 2^-24: only D < 0 is decided here
         t_lo = 0;
         t_hi = kNoReject;
         return;
@@ -117,46 +125,51 @@ __device__ __forceinline__ void accept_bracket(unsigned long long U, int e0, lon
     const float uf = fmaf((float)top, 0x1p-24f, (float)((uint32_t)(U >> 5) & 0xffffffu) * 0x1p-48f);
     const float Lf = -logf(uf);
     const float margin = (Lf + 1.0f) * 0x1p-18f;
-    const int k = 1075 - e0;  // ulp = 2^(e0 - 1075)
-    t_lo = scaled_floor(Lf - margin, k);
-    t_hi = scaled_ceil(Lf + margin, k) + 1;
+    const long long lo = scaled_floor(Lf - margin, k) - 1;
+    t_lo = lo > 0 ? lo : 0;
+    t_hi = scaled_ceil(Lf + margin, k) + 2;
 }
 
-// Binade of a, and the integer step ln f / ulp(a) if it is exact.
-struct Binade {
-    long long lo, hi;  // [lo, hi) bit patterns with exponent e0
-    long long inc;     // ln f in units of ulp(binade)
-    int e0;
-    bool add_ok;
-};
-__device__ __forceinline__ Binade binade_of(long long A, long long LNF) {
-    Binade b;
-    b.e0 = (int)(A >> 52);
-    b.lo = (long long)b.e0 << 52;
-    b.hi = (long long)(b.e0 + 1) << 52;
-    b.inc = 0;
-    b.add_ok = false;
-    if (LNF == 0) {
-        b.add_ok = true;
-    } else if (b.e0 > 0 && (LNF >> 52) > 0) {
-        const int el = (int)(LNF >> 52);
-        const long long ml = (LNF & ((1LL << 52) - 1)) | (1LL << 52);
-        const int sh = el - b.e0;
-        if (sh >= 0) {
-            if (sh <= 9) {
-                b.inc = ml << sh;
-                b.add_ok = b.inc < (1LL << 52);
-            }
-        } else if (sh > -53 && (ml & ((1LL << -sh) - 1)) == 0) {
-            b.inc = ml >> -sh;
-            b.add_ok = true;
-        }
+// floor(v / 2^(ew - 1075)) of a non-negative binary64 bit pattern v whose
+// exponent is at most ew + 10 (the result is then below 2^63).
+__device__ __forceinline__ long long fixed_floor(long long v, int ew) {
+    if (v == 0) return 0;
+    const int s = (int)(v >> 52) - ew;
+    const long long mf = (v & kMant) | kHidden;
+    if (s >= 0) return mf << s;
+    return s <= -63 ? 0 : (mf >> -s);
+}
+
+// v / 2^(e - 1075) for the binary64 value v = ln f if that is an integer below
+// 2^52 (ln f is an exact multiple of the unit and one step cannot span a
+// binade); ok = false otherwise.
+__device__ __forceinline__ long long exact_units(long long v, int e, bool &ok) {
+    ok = true;
+    if (v == 0) return 0;
+    const int el = (int)(v >> 52);
+    if (el == 0 || e <= 0) {
+        ok = false;
+        return 0;
     }
-    return b;
+    const long long mf = (v & kMant) | kHidden;
+    const int s = el - e;
+    if (s >= 0) {
+        if (s > 9) {
+            ok = false;
+            return 0;
+        }
+        const long long r = mf << s;
+        ok = r < (1LL << 52);
+        return r;
+    }
+    if (s <= -53 || (mf & ((1LL << -s) - 1)) != 0) {
+        ok = false;
+        return 0;
+    }
+    return mf >> -s;
 }
 
-// The reference decision in binary64: accept iff D >= 0 or u < exp(D),
-// D = a - b.
+// The reference decision in binary64: accept iff d >= 0 or u < exp(d), d = a - b.
 __device__ __noinline__ bool exact_accept(long long A, long long B, unsigned long long U, unsigned long long *ties) {
     const double d = __dsub_rn(__longlong_as_double(A), __longlong_as_double(B));
     if (d >= 0.0) return true;
@@ -179,100 +192,104 @@ __device__ __forceinline__ unsigned group_mask() {
 
 // Per-walker scratch of the lane group in shared memory (S > 1 only).
 struct Stage {
-    unsigned long long *pk;  // [S] packed proposal
-    long long *th;           // [2S] thresholds
-    unsigned long long *uu;  // [S] 53-bit uniforms
+    int4 *a;                 // [S] proposal: lattice word, new bits, keep mask, meta
+    longlong2 *th;           // [S] acceptance bracket (t_lo, t_hi)
+    unsigned long long *uu;  // [S] 53-bit uniforms (binary64 fallback only)
     uint32_t *bm;            // [ceil(N/32)] sites touched by this batch
 };
 
-// packed proposal: site (20 bits) | v (8) << 20 | cur (8) << 28 | new (8) << 36 |
-// (dE + 4) (4) << 44 | maybe-dirty (1) << 48
-__device__ __forceinline__ unsigned long long pack(int site, int v, int cur, int nw, int dE, bool maybe) {
-    return (unsigned long long)site | ((unsigned long long)v << 20) | ((unsigned long long)cur << 28) |
-           ((unsigned long long)nw << 36) | ((unsigned long long)(dE + 4) << 44) |
-           ((unsigned long long)(maybe ? 1 : 0) << 48);
+// Lattice write of one proposal as a word update: lat[w] = (lat[w] & keep) | bits.
+template <int BITS>
+__device__ __forceinline__ int4 proposal_word(int site, int nw) {
+    const int per = 32 / BITS;
+    const int sh = (site & (per - 1)) * BITS;
+    int4 a;
+    a.x = site / per;
+    a.y = (int)((uint32_t)nw << sh);
+    a.z = (int)~(((1u << BITS) - 1u) << sh);
+    a.w = 0;
+    return a;
 }
+// meta: dE + 8 in bits 0..3, maybe-dirty in bit 4, raw new-value draw v in bits 8..15
+__device__ __forceinline__ int meta_of(int dE, bool maybe, int v) { return (dE + 8) | ((maybe ? 1 : 0) << 4) | (v << 8); }
 
 struct Tally {
-    unsigned long long acc, ties, slow;
+    unsigned long long ties, slow;
+    unsigned int acc, seq;
 };
 
+constexpr long long kExactFloor = 1LL << 52;  // shadow values >= this are exact
+
+// Binary64 bits of the exact value F * 2^(ew - 1075), F >= 2^52.
+__device__ __forceinline__ long long from_fixed(long long F, int ew) {
+    const int sh = 11 - __clzll(F);  // top bit position - 52
+    return ((long long)(ew + sh) << 52) | ((F >> sh) & kMant);
+}
+
 template <int BITS, int S>
-__device__ void walker_sweep(const Model &M, uint32_t *lat, double *lg, uint32_t *hg, const Stage &st, int g, int lo,
+__device__ void walker_sweep(const Model &M, uint32_t *__restrict__ lat, long long *__restrict__ lgb,
+                             long long *__restrict__ lgf, uint32_t *__restrict__ hg, const Stage &st, int g, int lo,
                              double lnf, int &E_io, unsigned long long &t_io, Tally &tally) {
     const int j = (int)(threadIdx.x & (unsigned)(S - 1));
     const unsigned gm = group_mask<S>();
-    const int W = M.W, N = M.N, L = M.L;
+    const int N = M.N, L = M.L;
     const uint32_t qm1 = (uint32_t)(M.q - 1);
     const long long LNF = __double_as_longlong(lnf);
+
+    // ---- fixed-point frame of this launch --------------------------------------
+    long long vmax = 0;
+    for (int b = j; b < M.B; b += S) vmax = max(vmax, lgb[b]);
+#pragma unroll
+    for (int o = 1; o < S; o <<= 1) vmax = max(vmax, __shfl_xor_sync(gm, vmax, o));
+    const double reach = __dadd_rn(__longlong_as_double(vmax), __dmul_rn((double)M.K, lnf));
+    // values stay below 2^(e_reach + 2 - 1023): below 2^62 units of 2^(ew - 1075)
+    int ew = (int)(__double_as_longlong(reach) >> 52) - 8;
+    if (ew < 1) ew = 1;
+    const int k = 1075 - ew;
+    for (int b = j; b < M.B; b += S) lgf[b] = fixed_floor(lgb[b], ew);
+    for (int p = j; p < kPad; p += S) {
+        lgf[-1 - p] = kOutside;
+        lgf[M.B + p] = kOutside;
+    }
+    bool addF;
+    const long long incF = exact_units(LNF, ew, addF);
+    // every integer step inside a binade is exact when ln f is a multiple of the
+    // largest last place (2^10 units for values below 2^62 units)
+    const bool int_add = addF && (incF & 1023) == 0;
+    if (S > 1) __syncwarp(gm);
+
+    // State of the current bin: AF is its shadow, kept in lgf after every step.
+    // A shadow >= 2^52 is the value exactly; below that the exact binary64 bits
+    // are kept in lgb.  Steps on such small values, ln f steps that cross a
+    // binade, and decisions inside the bracket are done in binary64.
     int E = E_io;
     unsigned long long t = t_io;
-    long long A = __double_as_longlong(lg[E - lo]);
+    long long AF = lgf[E - lo];
     uint32_t visits = 0;
-    Binade bn = binade_of(A, LNF);
+    unsigned int nacc = 0;
 
     for (long long base = 0; base < M.K; base += S) {
         const int n = (int)((M.K - base) < S ? (M.K - base) : S);
-        // ---- parallel phase: lane j prepares proposal t + j ------------------
-        int site = N + j, v = 0, cur = 0, nw = 0, dE = 0;
+        // ---- parallel phase: lane j prepares proposal t + j --------------------
+        int site = N + j, v = 0, nw = 0, dE = 0;
         Site4 nb{0, 0, 0, 0};
-        long long tlo = 0, thi = kNoReject;
+        longlong2 th = make_longlong2(0, kNoReject);
         unsigned long long U = 0;
         if (j < n) {
             const unsigned long long tj = t + (unsigned long long)j;
             const uint4 r = philox((uint32_t)tj, (uint32_t)(tj >> 32), (uint32_t)g, DOM_WL, M.key0, M.key1);
             site = (int)__umulhi(r.x, (uint32_t)N);
             v = (int)__umulhi(r.y, qm1);
-            cur = spin_get<BITS>(lat, site);
+            const int cur = spin_get<BITS>(lat, site);
             nw = v + (v >= cur);
             nb = nbrs(site, L, N, M.divL);
             dE = energy_change<BITS>(lat, nb, cur, nw);
             U = u53(r.z, r.w);
-            accept_bracket(U, bn.e0, tlo, thi);
+            accept_bracket(U, k, th.x, th.y);
         }
-        if (S == 1) {
-            // ---- single lane: resolve directly --------------------------------
-            if (j < n) {
-                const int En = E + dE;
-                bool acc = false;
-                long long B = A;
-                if ((unsigned)(En - lo) <= (unsigned)W) {
-                    if (En == E) {
-                        acc = true;
-                    } else {
-                        B = __double_as_longlong(lg[En - lo]);
-                        if (B <= A) {
-                            acc = true;
-                        } else {
-                            const long long D = B - A;
-                            const bool fast = A >= bn.lo && B < bn.hi;
-                            if (fast && D < tlo) acc = true;
-                            else if (fast && D >= thi) acc = false;
-                            else {
-                                tally.slow += 1;
-                                acc = exact_accept(A, B, U, &tally.ties);
-                            }
-                        }
-                    }
-                }
-                if (acc) {
-                    spin_set<BITS>(lat, site, nw);
-                    tally.acc += 1;
-                    if (En != E) {
-                        lg[E - lo] = __longlong_as_double(A);
-                        hg[E - lo] += visits;
-                        E = En;
-                        A = B;
-                        visits = 0;
-                    }
-                }
-                const long long A2 = A + bn.inc;
-                if (bn.add_ok && A >= bn.lo && A2 < bn.hi) A = A2;
-                else A = exact_add(A, lnf);
-                visits += 1;
-            }
-        } else {
-            // ---- conflict marks: sites proposed in this batch -----------------
+        int4 a = proposal_word<BITS>(site, nw);
+        if (S > 1) {
+            // ---- conflict marks: sites proposed in this batch -------------------
             if (j < n) atomicOr(&st.bm[site >> 5], 1u << (site & 31));
             __syncwarp(gm);
             const unsigned peers = __match_any_sync(gm, site);
@@ -281,82 +298,108 @@ __device__ void walker_sweep(const Model &M, uint32_t *lat, double *lg, uint32_t
             if (j < n) {
                 maybe |= ((st.bm[nb.r >> 5] >> (nb.r & 31)) | (st.bm[nb.l >> 5] >> (nb.l & 31)) |
                           (st.bm[nb.d >> 5] >> (nb.d & 31)) | (st.bm[nb.u >> 5] >> (nb.u & 31))) & 1u;
-                st.pk[j] = pack(site, v, cur, nw, dE, maybe);
-                st.th[2 * j] = tlo;
-                st.th[2 * j + 1] = thi;
+                a.w = meta_of(dE, maybe, v);
+                st.a[j] = a;
+                st.th[j] = th;
                 st.uu[j] = U;
             }
             __syncwarp(gm);
             if (j < n) st.bm[site >> 5] = 0u;  // every marked word belongs to some lane's site
-            // ---- serial phase: the group resolves the proposals in order -------
-            bool any_acc = false;
-            for (int k = 0; k < n; ++k) {
-                const unsigned long long pk = st.pk[k];
-                int ks = (int)(pk & 0xfffffu);
-                int knw = (int)((pk >> 36) & 0xffu);
-                int kdE = (int)((pk >> 44) & 0xfu) - 4;
-                if (((pk >> 48) & 1ull) && any_acc) {  // neighbourhood changed in this batch
-                    const int kv = (int)((pk >> 20) & 0xffu);
-                    const int kc = spin_get<BITS>(lat, ks);
-                    knw = kv + (kv >= kc);
-                    kdE = energy_change<BITS>(lat, nbrs(ks, L, N, M.divL), kc, knw);
-                }
-                const int En = E + kdE;
-                bool acc = false;
-                long long B = A;
-                if ((unsigned)(En - lo) <= (unsigned)W) {
-                    if (En == E) {
-                        acc = true;
-                    } else {
-                        B = __double_as_longlong(lg[En - lo]);
-                        if (B <= A) {
-                            acc = true;
-                        } else {
-                            const long long D = B - A;
-                            const bool fast = A >= bn.lo && B < bn.hi;
-                            const long long klo = st.th[2 * k], khi = st.th[2 * k + 1];
-                            if (fast && D < klo) acc = true;
-                            else if (fast && D >= khi) acc = false;
-                            else {
-                                tally.slow += 1;
-                                acc = exact_accept(A, B, st.uu[k], &tally.ties);
-                            }
-                        }
-                    }
-                }
-                if (acc) {
-                    spin_set<BITS>(lat, ks, knw);
-                    any_acc = true;
-                    tally.acc += 1;
-                    if (En != E) {
-                        lg[E - lo] = __longlong_as_double(A);
-                        if (j == 0) hg[E - lo] += visits;
-                        E = En;
-                        A = B;
-                        visits = 0;
-                    }
-                }
-                const long long A2 = A + bn.inc;
-                if (bn.add_ok && A >= bn.lo && A2 < bn.hi) A = A2;
-                else A = exact_add(A, lnf);
-                visits += 1;
-            }
-            __syncwarp(gm);
+        } else {
+            a.w = meta_of(dE, false, v);
         }
+
+        // ---- serial phase: the group resolves the proposals in order ------------
+        bool any_acc = false;
+        int4 an = a;
+        longlong2 tn = th;
+        if (S > 1) {
+            an = st.a[0];
+            tn = st.th[0];
+        }
+        for (int kk = 0; kk < n; ++kk) {
+            int4 ka = an;
+            const longlong2 kt = tn;
+            if (S > 1) {  // next proposal's data, one step ahead (the staging arrays are padded)
+                an = st.a[kk + 1];
+                tn = st.th[kk + 1];
+            }
+            // ---- fast step: integer decision and ln f step, one branch to check --
+            int kdE = (ka.w & 15) - 8;
+            int En = E + kdE;
+            long long BF = lgf[En - lo];  // beyond the window: kOutside
+            long long D = BF - AF;
+            bool acc = D < kt.x;
+            long long cur = acc ? BF : AF;
+            long long AF2 = cur + incF;
+            const bool dirty = S > 1 && (ka.w & 16) && any_acc;
+            const bool cold = dirty || (!acc && D < kt.y) || cur < kExactFloor || (AF2 ^ cur) > cur || !int_add;
+            if (cold) {
+                // ---- the same step, every case done exactly -----------------------
+                if (dirty) {  // neighbourhood changed in this batch
+                    const int per = 32 / BITS;
+                    const int ks = ka.x * per + (__ffs(~ka.z) - 1) / BITS;
+                    const int kv = (ka.w >> 8) & 0xff;
+                    const int kc = spin_get<BITS>(lat, ks);
+                    const int knw = kv + (kv >= kc);
+                    kdE = energy_change<BITS>(lat, nbrs(ks, L, N, M.divL), kc, knw);
+                    ka = proposal_word<BITS>(ks, knw);
+                    En = E + kdE;
+                    BF = lgf[En - lo];
+                    D = BF - AF;
+                    acc = D < kt.x;
+                }
+                if (!acc && D < kt.y) {  // inside the bracket (never beyond the window)
+                    tally.slow += 1;
+                    const unsigned long long kU = S > 1 ? st.uu[kk] : U;
+                    const long long Ab = AF >= kExactFloor ? from_fixed(AF, ew) : lgb[E - lo];
+                    const long long Bb = BF >= kExactFloor ? from_fixed(BF, ew) : lgb[En - lo];
+                    acc = kdE == 0 ? true : exact_accept(Ab, Bb, kU, &tally.ties);
+                }
+                cur = acc ? BF : AF;  // with dE = 0, BF is the current shadow
+                AF2 = cur + incF;
+                if (!int_add || cur < kExactFloor || (AF2 ^ cur) > cur) {  // ln g(E) += ln f in binary64
+                    tally.seq += 1;
+                    const int Eb = acc ? En : E;
+                    const long long Ab = cur >= kExactFloor ? from_fixed(cur, ew) : lgb[Eb - lo];
+                    const long long A2 = exact_add(Ab, lnf);
+                    lgb[Eb - lo] = A2;
+                    AF2 = fixed_floor(A2, ew);
+                }
+            }
+            // ---- commit (predicated stores, no branches) --------------------------
+            const uint32_t word = lat[ka.x];
+            if (acc) lat[ka.x] = (word & (uint32_t)ka.z) | (uint32_t)ka.y;
+            const bool moved = acc && kdE != 0;
+            const uint32_t hv = hg[E - lo];
+            if (moved) hg[E - lo] = hv + visits;
+            visits = moved ? 1u : visits + 1u;
+            E = acc ? En : E;
+            AF = AF2;
+            lgf[E - lo] = AF;
+            any_acc |= acc;
+            nacc += acc ? 1u : 0u;
+        }
+        if (S > 1) __syncwarp(gm);
         t += (unsigned long long)n;
-        if ((A >> 52) != bn.e0) bn = binade_of(A, LNF);
     }
-    lg[E - lo] = __longlong_as_double(A);
-    if (j == 0) hg[E - lo] += visits;
+    hg[E - lo] += visits;
+    if (S > 1) __syncwarp(gm);
+    // the binary64 array from the authoritative shadow
+    for (int b = j; b < M.B; b += S) {
+        const long long F = lgf[b];
+        if (F >= kExactFloor) lgb[b] = from_fixed(F, ew);
+    }
+    tally.acc += nacc;
     E_io = E;
     t_io = t;
 }
 
 // Shared-memory layout of one walker.
 struct Layout {
-    int stride;           // bytes per walker (multiple of 16)
-    int off_H, off_lat;   // byte offsets (ln g at 0)
-    int off_pk, off_th, off_uu, off_bm;
+    int stride;                   // bytes per walker (multiple of 16)
+    int off_lgf, off_H, off_lat;  // byte offsets (ln g at 0)
+    int off_a, off_th, off_uu, off_bm;
 };
 
 template <int BITS, int S>
@@ -387,28 +430,30 @@ __global__ void __launch_bounds__(256) sweep_fast_kernel(Model M, State Sg, int 
     __syncthreads();
 
     const int grp = threadIdx.x / S, g = g0 + grp;
-    Tally tally{0ull, 0ull, 0ull};
+    Tally tally{0ull, 0ull, 0u, 0u};
     if (grp < P && g < M.G && !Sg.done[g / M.m]) {
         unsigned char *base = smem + (size_t)grp * lay.stride;
         Stage st;
-        st.pk = reinterpret_cast<unsigned long long *>(base + lay.off_pk);
-        st.th = reinterpret_cast<long long *>(base + lay.off_th);
+        st.a = reinterpret_cast<int4 *>(base + lay.off_a);
+        st.th = reinterpret_cast<longlong2 *>(base + lay.off_th);
         st.uu = reinterpret_cast<unsigned long long *>(base + lay.off_uu);
         st.bm = reinterpret_cast<uint32_t *>(base + lay.off_bm);
         const int w = g / M.m;
         const uint32_t c = Sg.slot_cfg[g];
         int E = Sg.cfg_E[c];
         unsigned long long t = Sg.t[g];
-        walker_sweep<BITS, S>(M, reinterpret_cast<uint32_t *>(base + lay.off_lat), reinterpret_cast<double *>(base),
+        walker_sweep<BITS, S>(M, reinterpret_cast<uint32_t *>(base + lay.off_lat), reinterpret_cast<long long *>(base),
+                              reinterpret_cast<long long *>(base + lay.off_lgf) + kPad,
                               reinterpret_cast<uint32_t *>(base + lay.off_H), st, g, Sg.e_lo[w], Sg.lnf[w], E, t,
                               tally);
         if ((threadIdx.x & (S - 1)) == 0) {
             Sg.cfg_E[c] = E;
             Sg.t[g] = t;
             atomicAdd(&Sg.ctl->flips, (unsigned long long)M.K);
-            atomicAdd(&Sg.ctl->accepted, tally.acc);
+            atomicAdd(&Sg.ctl->accepted, (unsigned long long)tally.acc);
             if (tally.slow) atomicAdd(&Sg.ctl->slow, tally.slow);
             if (tally.ties) atomicAdd(&Sg.ctl->ties, tally.ties);
+            if (tally.seq) atomicAdd(&Sg.ctl->seq, (unsigned long long)tally.seq);
         }
     }
     __syncthreads();
@@ -435,15 +480,17 @@ Layout make_layout(const Model &M, int S) {
     auto al = [](int x) { return (x + 15) & ~15; };
     Layout l{};
     int off = al(M.B * 8);
+    l.off_lgf = off;
+    off += al((M.B + 2 * kPad) * 8);
     l.off_H = off;
     off += al(M.B * 4);
     l.off_lat = off;
     off += al(M.wpc * 4);
-    if (S > 1) {
-        l.off_pk = off;
-        off += al(S * 8);
+    if (S > 1) {  // one spare entry: the serial loop reads one proposal ahead
+        l.off_a = off;
+        off += al((S + 1) * 16);
         l.off_th = off;
-        off += al(S * 16);
+        off += al((S + 1) * 16);
         l.off_uu = off;
         off += al(S * 8);
         l.off_bm = off;

@@ -101,6 +101,18 @@ def test_every_sweep_variant_matches(case, sweep):
         assert_parity(gpu, orc)
 
 
+@pytest.mark.parametrize("lanes", [1, 8, 32])
+def test_every_lane_width_converges_like_the_oracle(lanes):
+    """Whole runs through many ln f halvings and merges (binade changes of ln g,
+    exact-add fallbacks): identical final state for each lane-group width."""
+    from paper_1312_3004_gb300 import _lib
+    args = (3, 5, 3, 0.75, 3, 1e-4, 0.8, 777, 5)
+    gpu, orc = make_pair(*args, spin_bits=4)
+    gpu.set_option(_lib.OPT_LANES, lanes)
+    assert orc.run(0) and gpu.run(0)
+    assert_parity(gpu, orc)
+
+
 def test_first_million_updates_per_walker_ising_L8():
     """10^6 WL updates per walker (100 rounds of 10^4) on the L=8 Ising workload."""
     p = WL.params("ising_L8")
