@@ -213,6 +213,48 @@ rewl_status rewl_set_field(rewl_t h, int field, const void *in, size_t bytes);
 rewl_status rewl_save(rewl_t h, void *buf, size_t *len);
 rewl_status rewl_load(rewl_t h, const void *buf, size_t len);
 
+/* ---- Batches: many independent instances advanced together -----------------
+ * A batch holds n instances of uneven (q, L, h, m) in one device allocation.
+ * Each round runs one persistent sweep launch that takes walker groups of
+ * every unfinished instance from a device queue, one batched check launch
+ * (every window of every instance) and one batched exchange launch; rounds
+ * are replayed as a CUDA graph.  Every instance computes exactly the states it
+ * computes alone (same parameters, same seed): batching changes the runtime,
+ * not the arithmetic.  (Sec. 2's walkers and windows are independent between
+ * barriers; instances are independent altogether.) */
+typedef struct rewl_batch_s *rewl_batch_t;
+
+/* Create a batch of n instances (jobs[i] as in rewl_create; spin_bits as in
+ * rewl_create_ext, applied to all).  Errors as rewl_create, naming the job. */
+rewl_status rewl_batch_create(const rewl_params *jobs, int n, int spin_bits, rewl_batch_t *out);
+
+/* Run rounds of every unfinished instance until all have converged or
+ * max_rounds rounds were queued (<= 0: no limit); synchronises.
+ * *n_converged (may be NULL) = instances whose windows are all done. */
+rewl_status rewl_batch_run(rewl_batch_t b, long long max_rounds, int *n_converged);
+/* Queue `rounds` rounds without synchronising / read the status. */
+rewl_status rewl_batch_run_async(rewl_batch_t b, long long rounds);
+rewl_status rewl_batch_sync(rewl_batch_t b, int *n_converged);
+/* Stream for subsequent work (cudaStream_t as void*, NULL = own stream). */
+rewl_status rewl_batch_set_stream(rewl_batch_t b, void *stream);
+
+/* A read-only handle of instance i, owned by the batch: rewl_get_lng,
+ * rewl_get_window_lng, rewl_get_field, rewl_set_field, rewl_get_info,
+ * rewl_get_stats, rewl_save and rewl_load work on it; the functions that run
+ * rounds, change options or streams return REWL_ERR_STATE; rewl_destroy on it
+ * does nothing.  Valid until rewl_batch_destroy. */
+rewl_status rewl_batch_instance(rewl_batch_t b, int i, rewl_t *view);
+
+/* Sizes of a batch (each pointer may be NULL). */
+rewl_status rewl_batch_info(rewl_batch_t b, int *n_instances, long long *walkers, size_t *device_bytes);
+
+/* Counters summed over the instances (rounds = the largest round count;
+ * windows_done = converged instances; converged = all instances done). */
+rewl_status rewl_batch_stats(rewl_batch_t b, rewl_stats *stats);
+
+/* Release a batch and all of its instances.  NULL is ignored. */
+void rewl_batch_destroy(rewl_batch_t b);
+
 /* A whole run without allocating: for callers that cannot call cudaMalloc,
  * e.g. code under a framework whose caching allocator owns the device memory,
  * a process with a fixed device-memory budget, or a latency-critical loop that

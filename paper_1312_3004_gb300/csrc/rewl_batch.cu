@@ -1,0 +1,322 @@
+// rewl_batch.cu -- many independent REWL instances of uneven size (q, L, h, m)
+// in one device allocation, advanced together: one persistent sweep launch per
+// (spin bits, lanes) class takes walker groups of every instance from a device
+// queue, one batched check launch covers every window of every instance, one
+// batched exchange launch every instance; a CUDA graph replays these rounds.
+// Every instance computes exactly what it computes alone (its own Philox key,
+// its own state; the kernels run the same block code as the single-instance
+// launches).
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "rewl.h"
+#include "rewl_host_internal.hpp"
+#include "rewl_internal.cuh"
+
+using rewl::host::fail;
+
+namespace {
+
+constexpr int kBatchGraphRounds = 4;
+constexpr size_t kCtaBudget = 72 * 1024;  // shared memory per sweep CTA (3 CTAs per SM)
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+#define BATCH_CUDA(call)                                                                        \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess) return fail(REWL_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+struct SweepClass {
+    int bits = 4, lanes = 32, threads = 0, grid = 0;
+    size_t smem = 0;
+    std::vector<rewl::SweepItem> items;
+    rewl::SweepItem *d_items = nullptr;
+    unsigned int *d_queue = nullptr;
+};
+
+}  // namespace
+
+struct rewl_batch_s {
+    std::vector<rewl_s *> inst;
+    void *dmem = nullptr;
+    size_t dbytes = 0;
+    rewl::Ctl *h_ctls = nullptr;  // pinned mirrors of every instance's control block
+    rewl::Ctl *d_ctls = nullptr;  // the control blocks, contiguous
+    cudaStream_t own_stream = nullptr, stream = nullptr;
+    rewl::InstDev *d_inst = nullptr;
+    rewl::WinItem *d_wins = nullptr;
+    int n_wins = 0;
+    std::vector<SweepClass> classes;
+    unsigned int *d_queues = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    int sms = 0;
+};
+
+namespace {
+
+rewl_status enqueue_batch_round(rewl_batch_s *b, cudaStream_t s) {
+    BATCH_CUDA(cudaMemsetAsync(b->d_queues, 0, sizeof(unsigned int) * b->classes.size(), s));
+    for (auto &c : b->classes)
+        BATCH_CUDA(rewl::launch_batch_sweep(c.bits, c.lanes, b->d_inst, c.d_items, (int)c.items.size(), c.d_queue,
+                                            c.grid, c.threads, c.smem, s, false));
+    BATCH_CUDA(rewl::launch_batch_check(b->d_inst, b->d_wins, b->n_wins, s));
+    BATCH_CUDA(rewl::launch_batch_exchange(b->d_inst, (int)b->inst.size(), s));
+    return REWL_OK;
+}
+
+rewl_status build_batch_graph(rewl_batch_s *b) {
+    cudaStream_t cap;
+    BATCH_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    rewl_status st = REWL_OK;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        for (int r = 0; r < kBatchGraphRounds && st == REWL_OK; ++r) st = enqueue_batch_round(b, cap);
+        e = cudaStreamEndCapture(cap, &graph);
+    }
+    if (e == cudaSuccess && st == REWL_OK) e = cudaGraphInstantiate(&b->graph, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cap);
+    if (st) return st;
+    if (e != cudaSuccess) return fail(REWL_ERR_CUDA, "batch graph capture failed: %s", cudaGetErrorString(e));
+    return REWL_OK;
+}
+
+rewl_status enqueue_batch_rounds(rewl_batch_s *b, long long n) {
+    while (n >= kBatchGraphRounds) {
+        BATCH_CUDA(cudaGraphLaunch(b->graph, b->stream));
+        n -= kBatchGraphRounds;
+    }
+    for (; n > 0; --n) {
+        rewl_status st = enqueue_batch_round(b, b->stream);
+        if (st) return st;
+    }
+    return REWL_OK;
+}
+
+// Reads every control block; *done = number of converged instances.
+rewl_status read_batch_status(rewl_batch_s *b, int *done) {
+    const size_t n = b->inst.size();
+    BATCH_CUDA(cudaMemcpyAsync(b->h_ctls, b->d_ctls, n * sizeof(rewl::Ctl), cudaMemcpyDeviceToHost, b->stream));
+    BATCH_CUDA(cudaStreamSynchronize(b->stream));
+    int d = 0;
+    for (size_t i = 0; i < n; ++i) {
+        const rewl::Ctl &c = b->h_ctls[i];
+        if (c.error & rewl::ERR_OVERFLOW) return fail(REWL_ERR_OVERFLOW, "instance %zu: a histogram bin reached 2^31", i);
+        if (c.error & rewl::ERR_ENTRY) return fail(REWL_ERR_STATE, "instance %zu: a walker could not enter its window", i);
+        d += c.all_done ? 1 : 0;
+    }
+    if (done) *done = d;
+    return REWL_OK;
+}
+
+void destroy_batch(rewl_batch_s *b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (rewl_s *h : b->inst) delete h;
+    if (b->own_stream) cudaStreamDestroy(b->own_stream);
+    if (b->h_ctls) cudaFreeHost(b->h_ctls);
+    if (b->dmem) cudaFree(b->dmem);
+    delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+rewl_status rewl_batch_create(const rewl_params *jobs, int n, int spin_bits, rewl_batch_t *out) {
+    if (!jobs || !out || n < 1) return fail(REWL_ERR_ARG, "NULL argument or n < 1");
+    *out = nullptr;
+    rewl_batch_s *b = new rewl_batch_s();
+    auto cleanup = [&](rewl_status s) {
+        destroy_batch(b);
+        return s;
+    };
+    // ---- instances: parameters, sizes, plans (32 lanes per walker) -----------
+    size_t off = 0;
+    std::vector<size_t> inst_off((size_t)n);
+    for (int i = 0; i < n; ++i) {
+        rewl_s *h = new rewl_s();
+        h->owns = false;
+        b->inst.push_back(h);
+        rewl_status st = rewl::host::prepare_instance(h, jobs[i], spin_bits, 32);
+        if (st) return cleanup(fail(st, "job %d: %s", i, rewl_last_error()));
+        if ((size_t)h->plan.P < 1 || rewl::fast_smem_per_walker(h->M, 32) > (size_t)h->smem_optin)
+            return cleanup(fail(REWL_ERR_ARG, "job %d: a walker does not fit in shared memory", i));
+        inst_off[(size_t)i] = off;
+        off += align256(h->dbytes);
+    }
+    b->sms = b->inst[0]->sms;
+    // ---- tables -------------------------------------------------------------
+    std::vector<rewl::InstDev> tab((size_t)n);
+    std::vector<rewl::WinItem> wins;
+    for (int i = 0; i < n; ++i)
+        for (int w = 0; w < b->inst[(size_t)i]->M.h; ++w) wins.push_back({i, w});
+    b->n_wins = (int)wins.size();
+    for (int i = 0; i < n; ++i) {
+        rewl_s *h = b->inst[(size_t)i];
+        const rewl::Layout lay = rewl::fast_layout(h->M, 32);
+        int cls = -1;
+        for (size_t c = 0; c < b->classes.size(); ++c)
+            if (b->classes[c].bits == h->M.bits) cls = (int)c;
+        if (cls < 0) {
+            SweepClass c;
+            c.bits = h->M.bits;
+            c.lanes = 32;
+            b->classes.push_back(c);
+            cls = (int)b->classes.size() - 1;
+        }
+        SweepClass &c = b->classes[(size_t)cls];
+        int P = (int)(std::max(kCtaBudget, (size_t)lay.stride) / (size_t)lay.stride);
+        P = std::min(P, 256 / c.lanes);
+        for (int g0 = 0; g0 < h->M.G; g0 += P) c.items.push_back({i, g0, std::min(P, h->M.G - g0), 0});
+        c.smem = std::max(c.smem, (size_t)P * (size_t)lay.stride);
+        c.threads = std::max(c.threads, P * c.lanes);
+    }
+    const size_t off_ctl = off;
+    off += align256((size_t)n * sizeof(rewl::Ctl));
+    const size_t off_tab = off;
+    off += align256((size_t)n * sizeof(rewl::InstDev));
+    const size_t off_wins = off;
+    off += align256(wins.size() * sizeof(rewl::WinItem));
+    std::vector<size_t> off_items;
+    for (auto &c : b->classes) {
+        off_items.push_back(off);
+        off += align256(c.items.size() * sizeof(rewl::SweepItem));
+    }
+    const size_t off_q = off;
+    off += align256(b->classes.size() * sizeof(unsigned int));
+    b->dbytes = off;
+    cudaError_t e = cudaMalloc(&b->dmem, off);
+    if (e != cudaSuccess) return cleanup(fail(REWL_ERR_NOMEM, "cudaMalloc(%zu): %s", off, cudaGetErrorString(e)));
+    e = cudaStreamCreateWithFlags(&b->own_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cleanup(fail(REWL_ERR_CUDA, "stream: %s", cudaGetErrorString(e)));
+    b->stream = b->own_stream;
+    e = cudaMallocHost(&b->h_ctls, (size_t)n * sizeof(rewl::Ctl));
+    if (e != cudaSuccess) return cleanup(fail(REWL_ERR_NOMEM, "cudaMallocHost: %s", cudaGetErrorString(e)));
+    char *base = (char *)b->dmem;
+    b->d_ctls = (rewl::Ctl *)(base + off_ctl);
+    b->d_inst = (rewl::InstDev *)(base + off_tab);
+    b->d_wins = (rewl::WinItem *)(base + off_wins);
+    b->d_queues = (unsigned int *)(base + off_q);
+    // ---- carve and initialise every instance ---------------------------------
+    e = cudaMemsetAsync(b->d_ctls, 0, (size_t)n * sizeof(rewl::Ctl), b->stream);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        rewl_s *h = b->inst[(size_t)i];
+        rewl::host::carve_instance(h, base + inst_off[(size_t)i]);
+        h->S.ctl = b->d_ctls + i;  // control blocks contiguous: one status read for all
+        h->stream = b->stream;
+        h->h_ctl = b->h_ctls + i;
+        tab[(size_t)i].M = h->M;
+        tab[(size_t)i].S = h->S;
+        tab[(size_t)i].lay = rewl::fast_layout(h->M, 32);
+        e = rewl::host::init_instance_async(h, b->stream);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_inst, tab.data(), tab.size() * sizeof(rewl::InstDev), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_wins, wins.data(), wins.size() * sizeof(rewl::WinItem), cudaMemcpyHostToDevice, b->stream);
+    for (size_t c = 0; c < b->classes.size() && e == cudaSuccess; ++c) {
+        SweepClass &k = b->classes[c];
+        k.d_items = (rewl::SweepItem *)(base + off_items[c]);
+        k.d_queue = b->d_queues + c;
+        e = cudaMemcpyAsync(k.d_items, k.items.data(), k.items.size() * sizeof(rewl::SweepItem), cudaMemcpyHostToDevice,
+                            b->stream);
+        if (e != cudaSuccess) break;
+        e = rewl::launch_batch_sweep(k.bits, k.lanes, nullptr, nullptr, 0, nullptr, 0, k.threads, k.smem, nullptr, true);
+        if (e != cudaSuccess) break;
+        const int per_sm = std::max(1, rewl::batch_sweep_ctas_per_sm(k.bits, k.lanes, k.threads, k.smem));
+        k.grid = std::min((int)k.items.size(), per_sm * b->sms);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cleanup(fail(REWL_ERR_CUDA, "batch set-up: %s", cudaGetErrorString(e)));
+    rewl_status st = read_batch_status(b, nullptr);
+    if (st) return cleanup(st);
+    st = build_batch_graph(b);
+    if (st) return cleanup(st);
+    *out = b;
+    return REWL_OK;
+}
+
+void rewl_batch_destroy(rewl_batch_t b) { destroy_batch(b); }
+
+rewl_status rewl_batch_set_stream(rewl_batch_t b, void *stream) {
+    if (!b) return fail(REWL_ERR_ARG, "NULL batch");
+    BATCH_CUDA(cudaStreamSynchronize(b->stream));
+    b->stream = stream ? (cudaStream_t)stream : b->own_stream;
+    for (rewl_s *h : b->inst) h->stream = b->stream;
+    return REWL_OK;
+}
+
+rewl_status rewl_batch_run_async(rewl_batch_t b, long long rounds) {
+    if (!b) return fail(REWL_ERR_ARG, "NULL batch");
+    if (rounds < 0) return fail(REWL_ERR_ARG, "rounds < 0");
+    return enqueue_batch_rounds(b, rounds);
+}
+
+rewl_status rewl_batch_sync(rewl_batch_t b, int *n_converged) {
+    if (!b) return fail(REWL_ERR_ARG, "NULL batch");
+    return read_batch_status(b, n_converged);
+}
+
+rewl_status rewl_batch_run(rewl_batch_t b, long long max_rounds, int *n_converged) {
+    if (!b) return fail(REWL_ERR_ARG, "NULL batch");
+    const int n = (int)b->inst.size();
+    int done = 0;
+    rewl_status st = read_batch_status(b, &done);
+    long long left = max_rounds;
+    while (st == REWL_OK && done < n && (max_rounds <= 0 || left > 0)) {
+        const long long k = (max_rounds <= 0 || left >= kBatchGraphRounds) ? kBatchGraphRounds : left;
+        st = enqueue_batch_rounds(b, k);
+        if (st == REWL_OK) st = read_batch_status(b, &done);
+        left -= k;
+    }
+    if (n_converged) *n_converged = done;
+    return st;
+}
+
+rewl_status rewl_batch_instance(rewl_batch_t b, int i, rewl_t *view) {
+    if (!b || !view) return fail(REWL_ERR_ARG, "NULL argument");
+    if (i < 0 || i >= (int)b->inst.size()) return fail(REWL_ERR_ARG, "instance %d outside [0, %zu)", i, b->inst.size());
+    *view = b->inst[(size_t)i];
+    return REWL_OK;
+}
+
+rewl_status rewl_batch_info(rewl_batch_t b, int *n_instances, long long *walkers, size_t *device_bytes) {
+    if (!b) return fail(REWL_ERR_ARG, "NULL batch");
+    long long w = 0;
+    for (rewl_s *h : b->inst) w += h->M.G;
+    if (n_instances) *n_instances = (int)b->inst.size();
+    if (walkers) *walkers = w;
+    if (device_bytes) *device_bytes = b->dbytes;
+    return REWL_OK;
+}
+
+rewl_status rewl_batch_stats(rewl_batch_t b, rewl_stats *s) {
+    if (!b || !s) return fail(REWL_ERR_ARG, "NULL argument");
+    int done = 0;
+    rewl_status st = read_batch_status(b, &done);
+    std::memset(s, 0, sizeof *s);
+    s->min_lnf = 0.0;
+    s->max_lnf = 0.0;
+    for (size_t i = 0; i < b->inst.size(); ++i) {
+        const rewl::Ctl &c = b->h_ctls[i];
+        s->rounds = std::max(s->rounds, (long long)c.round);
+        s->flips += (long long)c.flips;
+        s->accepted += (long long)c.accepted;
+        s->exch_tried += (long long)c.xtried;
+        s->exch_accepted += (long long)c.xacc;
+        s->near_ties += (long long)c.ties;
+        s->slow_decisions += (long long)c.slow;
+        s->seq_steps += (long long)c.seq;
+    }
+    s->windows_done = done;  // instances, for a batch
+    s->converged = done == (int)b->inst.size() ? 1 : 0;
+    return st;
+}
+
+}  // extern "C"

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "rewl.h"
+#include "rewl_host_internal.hpp"
 #include "rewl_internal.cuh"
 
 using rewl::Ctl;
@@ -64,24 +65,17 @@ bool window_geometry(int L, int h, double o, std::vector<int32_t> &e_lo, int &W)
 
 void rewl::set_error(const char *msg) { g_last_error = msg; }
 
-struct rewl_s {
-    rewl_params prm{};
-    Model M{};
-    State S{};
-    rewl::SweepPlan plan{};
-    int device = 0;
-    cudaStream_t own_stream = nullptr;
-    cudaStream_t stream = nullptr;
-    void *dmem = nullptr;
-    size_t dbytes = 0;
-    Ctl *h_ctl = nullptr;  // pinned mirror of the device control block
-    std::vector<int32_t> e_lo;
-    cudaGraphExec_t graph = nullptr;
-    int sms = 0, smem_optin = 0;
-    // byte offsets of the state arrays inside dmem (for save / load)
-    struct Part { size_t off, bytes; };
-    std::vector<Part> parts;
-};
+rewl_status rewl::host::fail(rewl_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+
 
 namespace {
 
@@ -234,73 +228,60 @@ struct SaveHeader {
 
 }  // namespace
 
-// ============================================================================
-extern "C" {
 
-const char *rewl_last_error(void) { return g_last_error.c_str(); }
+namespace rewl {
+namespace host {
 
-const char *rewl_version(void) { return "rewl-gb300 0.1 (sm_103a)"; }
-
-rewl_status rewl_create_ext(const rewl_params *prm, int spin_bits, rewl_t *out) {
-    if (!prm || !out) return fail(REWL_ERR_ARG, "NULL argument");
-    *out = nullptr;
-    rewl_status st = check_params(*prm, spin_bits);
+rewl_status prepare_instance(rewl_s *h, const rewl_params &p, int spin_bits, int lanes) {
+    rewl_status st = check_params(p, spin_bits);
     if (st) return st;
     std::vector<int32_t> e_lo;
     int W = 0;
-    if (!window_geometry(prm->L, prm->h, prm->overlap, e_lo, W))
-        return fail(REWL_ERR_ARG, "window width below 8 bins (L=%d, h=%d, overlap=%g)", prm->L, prm->h, prm->overlap);
-
-    rewl_s *h = new rewl_s();
-    h->prm = *prm;
+    if (!window_geometry(p.L, p.h, p.overlap, e_lo, W))
+        return fail(REWL_ERR_ARG, "window width below 8 bins (L=%d, h=%d, overlap=%g)", p.L, p.h, p.overlap);
+    h->prm = p;
     h->e_lo = e_lo;
     Model &M = h->M;
-    M.q = prm->q;
-    M.L = prm->L;
-    M.N = prm->L * prm->L;
+    M.q = p.q;
+    M.L = p.L;
+    M.N = p.L * p.L;
     M.W = W;
     M.B = W + 1;
-    M.h = prm->h;
-    M.m = prm->m;
-    M.G = prm->h * prm->m;
-    M.bits = spin_bits ? spin_bits : (prm->q <= 16 ? 4 : 8);
+    M.h = p.h;
+    M.m = p.m;
+    M.G = p.h * p.m;
+    M.bits = spin_bits ? spin_bits : (p.q <= 16 ? 4 : 8);
     M.wpc = (M.N * M.bits + 31) / 32;
-    M.key0 = (uint32_t)(prm->seed & 0xffffffffull);
-    M.key1 = (uint32_t)(prm->seed >> 32);
-    M.divL = (uint32_t)((0x100000000ull + (unsigned long long)prm->L - 1) / (unsigned long long)prm->L);
-    M.K = prm->exchange_interval;
-    M.lnf_final = prm->lnf_final;
-    M.flatness = prm->flatness;
-
-    auto cleanup = [&](rewl_status s) {
-        rewl_destroy(h);
-        return s;
-    };
+    M.key0 = (uint32_t)(p.seed & 0xffffffffull);
+    M.key1 = (uint32_t)(p.seed >> 32);
+    M.divL = (uint32_t)((0x100000000ull + (unsigned long long)p.L - 1) / (unsigned long long)p.L);
+    M.K = p.exchange_interval;
+    M.lnf_final = p.lnf_final;
+    M.flatness = p.flatness;
     cudaError_t e = cudaGetDevice(&h->device);
-    if (e != cudaSuccess) return cleanup(fail(REWL_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e)));
-    int sms = 0, optin = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
-    h->sms = sms;
-    h->smem_optin = optin;
-    h->plan = rewl::plan_sweep(M, sms, (size_t)optin);
+    if (e != cudaSuccess) return fail(REWL_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
+    cudaDeviceGetAttribute(&h->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+    h->plan = rewl::plan_sweep(M, h->sms, (size_t)h->smem_optin, rewl::SWEEP_FAST, lanes);
     if (h->plan.P < 1)
-        return cleanup(fail(REWL_ERR_ARG, "one walker needs %zu bytes of shared memory (> %d)",
-                            rewl::fast_smem_per_walker(M, h->plan.lanes), optin));
-
-    // one allocation, carved into 256-byte aligned arrays
+        return fail(REWL_ERR_ARG, "one walker needs %zu bytes of shared memory (> %d)",
+                    rewl::fast_smem_per_walker(M, h->plan.lanes), h->smem_optin);
     const size_t G = (size_t)M.G, B = (size_t)M.B, hh = (size_t)M.h;
     const size_t sizes[] = {G * M.wpc * 4, G * 4, G * 4, G * 8, G * B * 8, G * B * 4, hh * B, hh * 4, hh * 8, hh * 4, hh,
                             sizeof(Ctl)};
     size_t off = 0;
-    for (size_t s : sizes) {
-        h->parts.push_back({off, s});
-        off += align256(s);
+    h->parts.clear();
+    for (size_t sz : sizes) {
+        h->parts.push_back({off, sz});
+        off += align256(sz);
     }
     h->dbytes = off;
-    e = cudaMalloc(&h->dmem, off);
-    if (e != cudaSuccess) return cleanup(fail(REWL_ERR_NOMEM, "cudaMalloc(%zu): %s", off, cudaGetErrorString(e)));
-    auto at = [&](int i) { return (void *)((char *)h->dmem + h->parts[(size_t)i].off); };
+    return REWL_OK;
+}
+
+void carve_instance(rewl_s *h, void *base) {
+    h->dmem = base;
+    auto at = [&](int i) { return (void *)((char *)base + h->parts[(size_t)i].off); };
     State &S = h->S;
     S.spins = (uint32_t *)at(0);
     S.cfg_E = (int32_t *)at(1);
@@ -314,20 +295,52 @@ rewl_status rewl_create_ext(const rewl_params *prm, int spin_bits, rewl_t *out) 
     S.iter = (int32_t *)at(9);
     S.done = (uint8_t *)at(10);
     S.ctl = (Ctl *)at(11);
+}
 
+cudaError_t init_instance_async(rewl_s *h, cudaStream_t s) {
+    const size_t hh = (size_t)h->M.h;
+    std::vector<double> lnf0(hh, 1.0);  // ln f_0 = 1
+    cudaError_t e = cudaMemsetAsync(h->dmem, 0, h->dbytes, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->S.e_lo, h->e_lo.data(), hh * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->S.lnf, lnf0.data(), hh * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // lnf0 lives on this stack frame
+    if (e == cudaSuccess) e = rewl::launch_init(h->M, h->S, s);
+    return e;
+}
+
+rewl_status read_status(rewl_s *h) { return read_ctl(h); }
+
+}  // namespace host
+}  // namespace rewl
+
+// ============================================================================
+extern "C" {
+
+const char *rewl_last_error(void) { return g_last_error.c_str(); }
+
+const char *rewl_version(void) { return "rewl-gb300 0.1 (sm_103a)"; }
+
+rewl_status rewl_create_ext(const rewl_params *prm, int spin_bits, rewl_t *out) {
+    if (!prm || !out) return fail(REWL_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    rewl_s *h = new rewl_s();
+    auto cleanup = [&](rewl_status s) {
+        rewl_destroy(h);
+        return s;
+    };
+    rewl_status st = rewl::host::prepare_instance(h, *prm, spin_bits, 0);
+    if (st) return cleanup(st);
+    cudaError_t e = cudaMalloc(&h->dmem, h->dbytes);
+    if (e != cudaSuccess)
+        return cleanup(fail(REWL_ERR_NOMEM, "cudaMalloc(%zu): %s", h->dbytes, cudaGetErrorString(e)));
+    rewl::host::carve_instance(h, h->dmem);
     e = cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cleanup(fail(REWL_ERR_CUDA, "stream: %s", cudaGetErrorString(e)));
     h->stream = h->own_stream;
     e = cudaMallocHost(&h->h_ctl, sizeof(Ctl));
     if (e != cudaSuccess) return cleanup(fail(REWL_ERR_NOMEM, "cudaMallocHost: %s", cudaGetErrorString(e)));
-
-    std::vector<double> lnf0(hh, 1.0);  // ln f_0 = 1
-    e = cudaMemsetAsync(h->dmem, 0, off, h->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(S.e_lo, e_lo.data(), hh * 4, cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(S.lnf, lnf0.data(), hh * 8, cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = rewl::launch_init(M, S, h->stream);
-    if (e == cudaSuccess) e = rewl::prepare_sweep(M, h->plan);
+    e = rewl::host::init_instance_async(h, h->stream);
+    if (e == cudaSuccess) e = rewl::prepare_sweep(h->M, h->plan);
     if (e != cudaSuccess) return cleanup(fail(REWL_ERR_CUDA, "initialisation: %s", cudaGetErrorString(e)));
     st = read_ctl(h);
     if (st) return cleanup(st);
@@ -353,7 +366,7 @@ rewl_status rewl_create(int q, int L, int h, double overlap, int m, double lnf_f
 }
 
 void rewl_destroy(rewl_t h) {
-    if (!h) return;
+    if (!h || !h->owns) return;  // instances of a batch belong to the batch
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->graph) cudaGraphExecDestroy(h->graph);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
@@ -363,6 +376,7 @@ void rewl_destroy(rewl_t h) {
 }
 
 rewl_status rewl_set_stream(rewl_t h, void *stream) {
+    if (h && !h->owns) return fail(REWL_ERR_STATE, "this instance belongs to a batch: run the batch");
     if (!h) return fail(REWL_ERR_ARG, "NULL handle");
     REWL_CUDA(cudaStreamSynchronize(h->stream));
     h->stream = stream ? (cudaStream_t)stream : h->own_stream;
@@ -370,12 +384,14 @@ rewl_status rewl_set_stream(rewl_t h, void *stream) {
 }
 
 rewl_status rewl_run_async(rewl_t h, long long rounds) {
+    if (h && !h->owns) return fail(REWL_ERR_STATE, "this instance belongs to a batch: run the batch");
     if (!h) return fail(REWL_ERR_ARG, "NULL handle");
     if (rounds < 0) return fail(REWL_ERR_ARG, "rounds < 0");
     return enqueue_rounds(h, rounds);
 }
 
 rewl_status rewl_run_phase(rewl_t h, int phase) {
+    if (h && !h->owns) return fail(REWL_ERR_STATE, "this instance belongs to a batch: run the batch");
     if (!h) return fail(REWL_ERR_ARG, "NULL handle");
     switch (phase) {
     case REWL_PHASE_SWEEP: REWL_CUDA(rewl::launch_sweep(h->M, h->S, h->plan, h->stream)); break;
@@ -387,6 +403,7 @@ rewl_status rewl_run_phase(rewl_t h, int phase) {
 }
 
 rewl_status rewl_set_option(rewl_t h, int option, long long value) {
+    if (h && !h->owns) return fail(REWL_ERR_STATE, "this instance belongs to a batch: run the batch");
     if (!h) return fail(REWL_ERR_ARG, "NULL handle");
     int kind = h->plan.kind, lanes = h->plan.lanes;
     if (option == REWL_OPT_SWEEP_KERNEL) {
@@ -429,6 +446,7 @@ rewl_status rewl_sync(rewl_t h, int *converged) {
 }
 
 rewl_status rewl_run(rewl_t h, long long max_rounds, int *converged) {
+    if (h && !h->owns) return fail(REWL_ERR_STATE, "this instance belongs to a batch: run the batch");
     if (!h) return fail(REWL_ERR_ARG, "NULL handle");
     long long left = max_rounds;
     rewl_status st = read_ctl(h);
@@ -597,8 +615,10 @@ rewl_status rewl_save(rewl_t h, void *buf, size_t *len) {
     }
     if (*len < need) return fail(REWL_ERR_ARG, "buffer of %zu bytes < %zu", *len, need);
     unsigned char *dst = (unsigned char *)buf + sizeof(SaveHeader);
-    for (auto &p : h->parts) {
-        REWL_CUDA(cudaMemcpyAsync(dst, (char *)h->dmem + p.off, p.bytes, cudaMemcpyDeviceToHost, h->stream));
+    for (size_t i = 0; i < h->parts.size(); ++i) {
+        const auto &p = h->parts[i];
+        const void *src = i + 1 == h->parts.size() ? (const void *)h->S.ctl : (const void *)((char *)h->dmem + p.off);
+        REWL_CUDA(cudaMemcpyAsync(dst, src, p.bytes, cudaMemcpyDeviceToHost, h->stream));
         dst += p.bytes;
     }
     REWL_CUDA(cudaStreamSynchronize(h->stream));
@@ -629,8 +649,10 @@ rewl_status rewl_load(rewl_t h, const void *buf, size_t len) {
     if (fnv1a((const unsigned char *)buf + sizeof(SaveHeader), payload) != hd.checksum)
         return fail(REWL_ERR_ARG, "blob checksum mismatch (corrupted)");
     const unsigned char *src = (const unsigned char *)buf + sizeof(SaveHeader);
-    for (auto &p : h->parts) {
-        REWL_CUDA(cudaMemcpyAsync((char *)h->dmem + p.off, src, p.bytes, cudaMemcpyHostToDevice, h->stream));
+    for (size_t i = 0; i < h->parts.size(); ++i) {
+        const auto &p = h->parts[i];
+        void *dst = i + 1 == h->parts.size() ? (void *)h->S.ctl : (void *)((char *)h->dmem + p.off);
+        REWL_CUDA(cudaMemcpyAsync(dst, src, p.bytes, cudaMemcpyHostToDevice, h->stream));
         src += p.bytes;
     }
     REWL_CUDA(cudaStreamSynchronize(h->stream));

@@ -1,0 +1,48 @@
+// rewl_host_internal.hpp -- host-side instance record shared by the
+// single-instance driver (rewl_host.cu) and the batch engine (rewl_batch.cu).
+#pragma once
+#include <vector>
+
+#include "rewl.h"
+#include "rewl_internal.cuh"
+
+struct rewl_s {
+    rewl_params prm{};
+    rewl::Model M{};
+    rewl::State S{};
+    rewl::SweepPlan plan{};
+    int device = 0;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    void *dmem = nullptr;  // base of this instance's device arrays
+    size_t dbytes = 0;
+    rewl::Ctl *h_ctl = nullptr;  // pinned mirror of the device control block
+    std::vector<int32_t> e_lo;
+    cudaGraphExec_t graph = nullptr;
+    int sms = 0, smem_optin = 0;
+    // byte offsets of the state arrays relative to dmem (for save / load); the
+    // last part is the control block
+    struct Part { size_t off, bytes; };
+    std::vector<Part> parts;
+    // false for an instance that lives inside a batch: the batch owns its
+    // memory, stream and pinned status block, and runs its rounds
+    bool owns = true;
+};
+
+namespace rewl {
+namespace host {
+
+// Checks the parameters, computes the window table and the sizes of the device
+// arrays (h->parts, h->dbytes) and plans the sweep.  lanes: lanes per walker of
+// the fast sweep (0 = from the walker count).  No device memory is touched.
+rewl_status prepare_instance(rewl_s *h, const rewl_params &p, int spin_bits, int lanes);
+// Points h->S at the arrays of a region of h->dbytes bytes at `base`.
+void carve_instance(rewl_s *h, void *base);
+// Queues zeroing, the window table, ln f = 1 and the initial configurations.
+cudaError_t init_instance_async(rewl_s *h, cudaStream_t s);
+// Reads the control block (synchronises h->stream) and maps its error bits.
+rewl_status read_status(rewl_s *h);
+rewl_status fail(rewl_status st, const char *fmt, ...);
+
+}  // namespace host
+}  // namespace rewl

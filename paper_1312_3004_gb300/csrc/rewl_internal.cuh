@@ -62,6 +62,28 @@ struct State {
 
 enum : int { SWEEP_REFERENCE = 0, SWEEP_FAST = 1 };
 
+// Shared-memory layout of one walker in the fast sweep.
+struct Layout {
+    int stride;                   // bytes per walker (multiple of 16)
+    int off_lgf, off_H, off_lat;  // byte offsets (ln g at 0)
+    int off_a, off_th, off_uu, off_bm;
+};
+
+// One instance of a batch, as the batched kernels see it.
+struct InstDev {
+    Model M;
+    State S;
+    Layout lay;   // fast-sweep layout of this instance's walkers
+};
+// A piece of sweep work: P walkers g0 .. g0 + P - 1 of one instance.
+struct SweepItem {
+    int inst, g0, P, pad;
+};
+// A window of one instance for the batched check.
+struct WinItem {
+    int inst, w;
+};
+
 struct SweepPlan {
     int kind;        // SWEEP_REFERENCE (binary64 on the chain) or SWEEP_FAST
     int lanes;       // lanes per walker of the fast sweep (1, 2, 4, 8, 16, 32)
@@ -85,6 +107,16 @@ cudaError_t launch_get_spins(const Model &M, const State &S, uint8_t *spins_dev,
 size_t sweep_smem_per_walker(const Model &M);
 size_t fast_smem_per_walker(const Model &M, int lanes);
 cudaError_t launch_sweep_fast(const Model &M, const State &S, const SweepPlan &p, cudaStream_t s, bool prepare);
+
+Layout fast_layout(const Model &M, int lanes);
+cudaError_t launch_batch_check(const InstDev *inst, const WinItem *wins, int n_wins, cudaStream_t s);
+cudaError_t launch_batch_exchange(const InstDev *inst, int n_inst, cudaStream_t s);
+// Persistent batched sweep for one (spin bits, lanes) class: CTAs of `threads`
+// threads with `smem` bytes take items from *queue until n_items are done.
+cudaError_t launch_batch_sweep(int bits, int lanes, const InstDev *inst, const SweepItem *items, int n_items,
+                               unsigned int *queue, int grid, int threads, size_t smem, cudaStream_t s,
+                               bool prepare);
+int batch_sweep_ctas_per_sm(int bits, int lanes, int threads, size_t smem);
 
 // Record the message returned by rewl_last_error() on this thread (rewl_host.cu).
 void set_error(const char *msg);

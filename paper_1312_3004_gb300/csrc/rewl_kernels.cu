@@ -244,9 +244,8 @@ __global__ void __launch_bounds__(256) sweep_kernel(Model M, State S, int P) {
 constexpr int MAX_M = 256;  // walkers per window (exchange permutation buffer)
 constexpr int CHECK_THREADS = 256;
 
-__global__ void __launch_bounds__(CHECK_THREADS) window_check_kernel(Model M, State S) {
+__device__ void window_check_block(const Model &M, const State &S, int w) {
     if (*(volatile unsigned int *)&S.ctl->all_done) return;
-    const int w = blockIdx.x;
     if (S.done[w]) return;
     const int B = M.B, m = M.m, tid = threadIdx.x;
     const size_t base = (size_t)w * m * B;
@@ -330,6 +329,10 @@ __global__ void __launch_bounds__(CHECK_THREADS) window_check_kernel(Model M, St
     }
 }
 
+__global__ void __launch_bounds__(CHECK_THREADS) window_check_kernel(Model M, State S) {
+    window_check_block(M, S, blockIdx.x);
+}
+
 // ---------------------------------------------------------------------------
 // Barrier part 2, one CTA (Sec. 2, Eq. 1): for every window pair (a, a+1)
 // with a = round mod 2 and neither window finished, walker k of window a is
@@ -341,7 +344,7 @@ __global__ void __launch_bounds__(CHECK_THREADS) window_check_kernel(Model M, St
 // Then the round counter advances and the completion flag is refreshed.
 constexpr int XCH_THREADS = 1024;
 
-__global__ void __launch_bounds__(XCH_THREADS) exchange_kernel(Model M, State S) {
+__device__ void exchange_block(const Model &M, const State &S) {
     __shared__ int perm[XCH_THREADS / 32][MAX_M];
     Ctl *ctl = S.ctl;
     if (*(volatile unsigned int *)&ctl->all_done) return;
@@ -396,6 +399,24 @@ __global__ void __launch_bounds__(XCH_THREADS) exchange_kernel(Model M, State S)
         for (int w = 0; w < M.h; ++w) all &= (unsigned int)(S.done[w] != 0);
         ctl->all_done = all;
     }
+}
+
+__global__ void __launch_bounds__(XCH_THREADS) exchange_kernel(Model M, State S) { exchange_block(M, S); }
+
+// ---------------------------------------------------------------------------
+// Batched forms: many independent instances in one launch.  Every CTA looks up
+// its instance in a device table and runs the same block code as above.
+__global__ void __launch_bounds__(CHECK_THREADS) batch_check_kernel(const InstDev *inst, const WinItem *wins) {
+    const WinItem it = wins[blockIdx.x];
+    const Model M = inst[it.inst].M;
+    const State S = inst[it.inst].S;
+    window_check_block(M, S, it.w);
+}
+
+__global__ void __launch_bounds__(XCH_THREADS) batch_exchange_kernel(const InstDev *inst) {
+    const Model M = inst[blockIdx.x].M;
+    const State S = inst[blockIdx.x].S;
+    exchange_block(M, S);
 }
 
 // ---------------------------------------------------------------------------
@@ -496,6 +517,18 @@ cudaError_t launch_window_check(const Model &M, const State &S, cudaStream_t s) 
 
 cudaError_t launch_exchange(const Model &M, const State &S, cudaStream_t s) {
     exchange_kernel<<<1, XCH_THREADS, 0, s>>>(M, S);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_check(const InstDev *inst, const WinItem *wins, int n_wins, cudaStream_t s) {
+    if (n_wins <= 0) return cudaSuccess;
+    batch_check_kernel<<<n_wins, CHECK_THREADS, 0, s>>>(inst, wins);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_exchange(const InstDev *inst, int n_inst, cudaStream_t s) {
+    if (n_inst <= 0) return cudaSuccess;
+    batch_exchange_kernel<<<n_inst, XCH_THREADS, 0, s>>>(inst);
     return cudaGetLastError();
 }
 

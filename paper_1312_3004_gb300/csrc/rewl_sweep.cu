@@ -395,18 +395,11 @@ __device__ void walker_sweep(const Model &M, uint32_t *__restrict__ lat, long lo
     t_io = t;
 }
 
-// Shared-memory layout of one walker.
-struct Layout {
-    int stride;                   // bytes per walker (multiple of 16)
-    int off_lgf, off_H, off_lat;  // byte offsets (ln g at 0)
-    int off_a, off_th, off_uu, off_bm;
-};
-
+// P walkers g0 .. g0 + P - 1 of one instance: stage their state in shared
+// memory, run K steps (one lane group per walker), write the state back.
 template <int BITS, int S>
-__global__ void __launch_bounds__(256) sweep_fast_kernel(Model M, State Sg, int P, Layout lay) {
-    extern __shared__ __align__(16) unsigned char smem[];
+__device__ void sweep_block(const Model &M, const State &Sg, int g0, int P, const Layout &lay, unsigned char *smem) {
     if (*(volatile unsigned int *)&Sg.ctl->all_done) return;
-    const int g0 = blockIdx.x * P;
     for (int p = 0; p < P; ++p) {
         const int g = g0 + p;
         if (g >= M.G || Sg.done[g / M.m]) continue;
@@ -476,6 +469,32 @@ __global__ void __launch_bounds__(256) sweep_fast_kernel(Model M, State Sg, int 
     }
 }
 
+template <int BITS, int S>
+__global__ void __launch_bounds__(256) sweep_fast_kernel(Model M, State Sg, int P, Layout lay) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    sweep_block<BITS, S>(M, Sg, blockIdx.x * P, P, lay, smem);
+}
+
+// Persistent batched sweep: each CTA takes the next item from *queue.
+template <int BITS, int S>
+__global__ void __launch_bounds__(256) batch_sweep_kernel(const InstDev *inst, const SweepItem *items, int n_items,
+                                                          unsigned int *queue) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int next;
+    for (;;) {
+        if (threadIdx.x == 0) next = (int)atomicAdd(queue, 1u);
+        __syncthreads();
+        const int i = next;
+        if (i >= n_items) break;
+        const SweepItem it = items[i];
+        const Model M = inst[it.inst].M;
+        const State Sg = inst[it.inst].S;
+        const Layout lay = inst[it.inst].lay;
+        sweep_block<BITS, S>(M, Sg, it.g0, it.P, lay, smem);
+        __syncthreads();
+    }
+}
+
 Layout make_layout(const Model &M, int S) {
     auto al = [](int x) { return (x + 15) & ~15; };
     Layout l{};
@@ -525,6 +544,69 @@ cudaError_t dispatch_s(const Model &M, const State &St, const SweepPlan &p, cuda
 }  // namespace fast
 
 size_t fast_smem_per_walker(const Model &M, int lanes) { return (size_t)fast::make_layout(M, lanes).stride; }
+
+Layout fast_layout(const Model &M, int lanes) { return fast::make_layout(M, lanes); }
+
+namespace {
+template <int BITS, int S>
+cudaError_t batch_launch_t(const InstDev *inst, const SweepItem *items, int n_items, unsigned int *queue, int grid,
+                           int threads, size_t smem, cudaStream_t s, bool prepare) {
+    if (prepare)
+        return cudaFuncSetAttribute(fast::batch_sweep_kernel<BITS, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem);
+    if (n_items <= 0) return cudaSuccess;
+    fast::batch_sweep_kernel<BITS, S><<<grid, threads, smem, s>>>(inst, items, n_items, queue);
+    return cudaGetLastError();
+}
+template <int BITS>
+cudaError_t batch_dispatch(int lanes, const InstDev *inst, const SweepItem *items, int n_items, unsigned int *queue,
+                           int grid, int threads, size_t smem, cudaStream_t s, bool prepare) {
+    switch (lanes) {
+    case 1: return batch_launch_t<BITS, 1>(inst, items, n_items, queue, grid, threads, smem, s, prepare);
+    case 2: return batch_launch_t<BITS, 2>(inst, items, n_items, queue, grid, threads, smem, s, prepare);
+    case 4: return batch_launch_t<BITS, 4>(inst, items, n_items, queue, grid, threads, smem, s, prepare);
+    case 8: return batch_launch_t<BITS, 8>(inst, items, n_items, queue, grid, threads, smem, s, prepare);
+    case 16: return batch_launch_t<BITS, 16>(inst, items, n_items, queue, grid, threads, smem, s, prepare);
+    default: return batch_launch_t<BITS, 32>(inst, items, n_items, queue, grid, threads, smem, s, prepare);
+    }
+}
+template <int BITS, int S>
+int occupancy_t(int threads, size_t smem) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fast::batch_sweep_kernel<BITS, S>, threads, smem) !=
+        cudaSuccess)
+        return 0;
+    return n;
+}
+}  // namespace
+
+cudaError_t launch_batch_sweep(int bits, int lanes, const InstDev *inst, const SweepItem *items, int n_items,
+                               unsigned int *queue, int grid, int threads, size_t smem, cudaStream_t s,
+                               bool prepare) {
+    return bits == 8 ? batch_dispatch<8>(lanes, inst, items, n_items, queue, grid, threads, smem, s, prepare)
+                     : batch_dispatch<4>(lanes, inst, items, n_items, queue, grid, threads, smem, s, prepare);
+}
+
+int batch_sweep_ctas_per_sm(int bits, int lanes, int threads, size_t smem) {
+    if (bits == 8) {
+        switch (lanes) {
+        case 1: return occupancy_t<8, 1>(threads, smem);
+        case 2: return occupancy_t<8, 2>(threads, smem);
+        case 4: return occupancy_t<8, 4>(threads, smem);
+        case 8: return occupancy_t<8, 8>(threads, smem);
+        case 16: return occupancy_t<8, 16>(threads, smem);
+        default: return occupancy_t<8, 32>(threads, smem);
+        }
+    }
+    switch (lanes) {
+    case 1: return occupancy_t<4, 1>(threads, smem);
+    case 2: return occupancy_t<4, 2>(threads, smem);
+    case 4: return occupancy_t<4, 4>(threads, smem);
+    case 8: return occupancy_t<4, 8>(threads, smem);
+    case 16: return occupancy_t<4, 16>(threads, smem);
+    default: return occupancy_t<4, 32>(threads, smem);
+    }
+}
 
 cudaError_t launch_sweep_fast(const Model &M, const State &S, const SweepPlan &p, cudaStream_t s, bool prepare) {
     return M.bits == 8 ? fast::dispatch_s<8>(M, S, p, s, prepare) : fast::dispatch_s<4>(M, S, p, s, prepare);

@@ -35,11 +35,15 @@ class REWL:
     """
 
     def __init__(self, q, L, h, overlap, m, lnf_final, flatness, exchange_interval, seed,
-                 spin_bits=0, stream=None):
+                 spin_bits=0, stream=None, _view=None):
         self._L = _lib.load()
-        self._h = C.c_void_p()
-        p = _lib.Params(q, L, h, overlap, m, lnf_final, flatness, exchange_interval, seed)
-        check(self._L.rewl_create_ext(C.byref(p), spin_bits, C.byref(self._h)))
+        self._owner = None
+        if _view is not None:  # an instance owned by a Batch
+            self._h, self._owner = _view
+        else:
+            self._h = C.c_void_p()
+            p = _lib.Params(q, L, h, overlap, m, lnf_final, flatness, exchange_interval, seed)
+            check(self._L.rewl_create_ext(C.byref(p), spin_bits, C.byref(self._h)))
         info = _lib.Info()
         check(self._L.rewl_get_info(self._h, C.byref(info)))
         self.q, self.L, self.h, self.m = q, L, h, m
@@ -51,9 +55,9 @@ class REWL:
             self.set_stream(stream)
 
     def close(self):
-        if getattr(self, "_h", None) and self._h.value:
+        if getattr(self, "_owner", None) is None and getattr(self, "_h", None) and self._h.value:
             self._L.rewl_destroy(self._h)
-            self._h = C.c_void_p()
+        self._h = C.c_void_p()
 
     def __del__(self):
         try:
@@ -139,3 +143,79 @@ class REWL:
     def load(self, blob):
         buf = C.create_string_buffer(bytes(blob), len(blob))
         check(self._L.rewl_load(self._h, buf, len(blob)))
+
+
+class Batch:
+    """Many independent REWL instances advanced together (one persistent sweep
+    launch, one batched check and one batched exchange launch per round).
+
+    jobs: sequence of dicts with the REWL parameters (q, L, h, overlap, m,
+    lnf_final, flatness, exchange_interval, seed).  Each instance computes the
+    same states as it would alone.
+    """
+
+    def __init__(self, jobs, spin_bits=0, stream=None):
+        self._L = _lib.load()
+        self._h = C.c_void_p()
+        self.jobs = [dict(j) for j in jobs]
+        arr = (_lib.Params * len(self.jobs))()
+        for i, j in enumerate(self.jobs):
+            arr[i] = _lib.Params(j["q"], j["L"], j["h"], j["overlap"], j["m"], j["lnf_final"],
+                                 j["flatness"], j["exchange_interval"], j["seed"])
+        check(self._L.rewl_batch_create(arr, len(self.jobs), spin_bits, C.byref(self._h)))
+        if stream is not None:
+            self.set_stream(stream)
+        self._views = {}
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            for v in self._views.values():
+                v._h = C.c_void_p()
+            self._L.rewl_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __len__(self):
+        return len(self.jobs)
+
+    def set_stream(self, stream):
+        raw = getattr(stream, "cuda_stream", stream)
+        check(self._L.rewl_batch_set_stream(self._h, C.c_void_p(raw) if raw else None))
+
+    def run(self, max_rounds=0):
+        n = C.c_int(0)
+        check(self._L.rewl_batch_run(self._h, max_rounds, C.byref(n)))
+        return n.value
+
+    def run_async(self, rounds):
+        check(self._L.rewl_batch_run_async(self._h, rounds))
+
+    def sync(self):
+        n = C.c_int(0)
+        check(self._L.rewl_batch_sync(self._h, C.byref(n)))
+        return n.value
+
+    def instance(self, i):
+        """Read-only REWL handle of instance i (owned by the batch)."""
+        if i not in self._views:
+            v = C.c_void_p()
+            check(self._L.rewl_batch_instance(self._h, i, C.byref(v)))
+            j = self.jobs[i]
+            self._views[i] = REWL(j["q"], j["L"], j["h"], j["overlap"], j["m"], j["lnf_final"],
+                                  j["flatness"], j["exchange_interval"], j["seed"], _view=(v, self))
+        return self._views[i]
+
+    def info(self):
+        n, w, b = C.c_int(0), C.c_longlong(0), C.c_size_t(0)
+        check(self._L.rewl_batch_info(self._h, C.byref(n), C.byref(w), C.byref(b)))
+        return {"instances": n.value, "walkers": w.value, "device_bytes": b.value}
+
+    def stats(self):
+        s = _lib.Stats()
+        check(self._L.rewl_batch_stats(self._h, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in _lib.Stats._fields_}
