@@ -255,6 +255,45 @@ rewl_status rewl_batch_stats(rewl_batch_t b, rewl_stats *stats);
 /* Release a batch and all of its instances.  NULL is ignored. */
 void rewl_batch_destroy(rewl_batch_t b);
 
+/* ---- Serving: continuous batching of density-of-states jobs -----------------
+ * A server owns a device memory pool of pool_bytes and at most max_jobs
+ * resident jobs.  Submitted jobs wait in a first-come queue until their state
+ * fits into the pool (admission by device footprint; a later, smaller job may
+ * be admitted before an earlier one that does not fit yet).  Each
+ * rewl_server_step admits what fits, advances every resident job by `rounds`
+ * exchange rounds together (the batched kernels), and retires converged jobs:
+ * their windows are joined on the host (Fig. 2 of the paper), the normalised
+ * ln g is kept by the server, and their memory returns to the pool.  A job
+ * computes exactly the states it computes when run alone.  Calls on one server
+ * are not thread-safe. */
+typedef struct rewl_server_s *rewl_server_t;
+enum { REWL_JOB_QUEUED = 0, REWL_JOB_RUNNING = 1, REWL_JOB_DONE = 2, REWL_JOB_FAILED = 3, REWL_JOB_CANCELLED = 4 };
+
+/* Errors: REWL_ERR_ARG (pool_bytes < 4096 or max_jobs < 1), REWL_ERR_NOMEM. */
+rewl_status rewl_server_create(size_t pool_bytes, int max_jobs, rewl_server_t *out);
+/* Queue a job (parameters as rewl_create_ext).  *job_id (may be NULL) names it.
+ * Errors: REWL_ERR_ARG (parameters), REWL_ERR_NOMEM (larger than the pool). */
+rewl_status rewl_server_submit(rewl_server_t s, const rewl_params *params, int spin_bits, long long *job_id);
+/* Admit, advance every resident job by rounds (>= 1) rounds, retire; then
+ * *n_running / *n_queued (may be NULL) count resident and waiting jobs. */
+rewl_status rewl_server_step(rewl_server_t s, long long rounds, int *n_running, int *n_queued);
+/* *state = REWL_JOB_*. */
+rewl_status rewl_server_poll(rewl_server_t s, long long job_id, int *state);
+/* Joined, normalised ln g of a finished job into `out` (host, 2N + 1 doubles,
+ * as rewl_get_lng).  Errors: REWL_ERR_STATE (not finished), REWL_ERR_CANCELLED,
+ * the job's own error if it failed, REWL_ERR_ARG (unknown job, wrong len). */
+rewl_status rewl_server_result(rewl_server_t s, long long job_id, double *out, size_t len);
+/* times (may be NULL): [submitted, admitted, finished] in seconds of a steady
+ * host clock; counts (may be NULL): [rounds, WL proposals, device bytes]. */
+rewl_status rewl_server_job_info(rewl_server_t s, long long job_id, double *times, long long *counts);
+/* Cancel a queued or running job (its memory returns to the pool). */
+rewl_status rewl_server_cancel(rewl_server_t s, long long job_id);
+/* counts (may be NULL): [queued, running, done, failed or cancelled, rounds
+ * stepped, WL proposals]; *pool_free (may be NULL): free pool bytes. */
+rewl_status rewl_server_info(rewl_server_t s, long long *counts, size_t *pool_free);
+/* Release the server, its pool and every job.  NULL is ignored. */
+void rewl_server_destroy(rewl_server_t s);
+
 /* A whole run without allocating: for callers that cannot call cudaMalloc,
  * e.g. code under a framework whose caching allocator owns the device memory,
  * a process with a fixed device-memory budget, or a latency-critical loop that

@@ -6,6 +6,6 @@ The computation runs in the CUDA library behind include/rewl.h
 only marshals arguments.
 """
 from ._lib import RewlError, load  # noqa: F401
-from .rewl import REWL, Batch  # noqa: F401
+from .rewl import REWL, Batch, Server  # noqa: F401
 
-__all__ = ["REWL", "Batch", "RewlError", "load"]
+__all__ = ["REWL", "Batch", "Server", "RewlError", "load"]

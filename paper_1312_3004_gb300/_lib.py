@@ -93,6 +93,19 @@ def load():
     for name in ("rewl_batch_create", "rewl_batch_run", "rewl_batch_run_async", "rewl_batch_sync",
                  "rewl_batch_set_stream", "rewl_batch_instance", "rewl_batch_info", "rewl_batch_stats"):
         getattr(L, name).restype = st
+    L.rewl_server_create.argtypes = [sz, i32, C.POINTER(H)]
+    L.rewl_server_submit.argtypes = [H, C.POINTER(Params), i32, C.POINTER(C.c_longlong)]
+    L.rewl_server_step.argtypes = [H, ll, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.rewl_server_poll.argtypes = [H, ll, C.POINTER(C.c_int)]
+    L.rewl_server_result.argtypes = [H, ll, vp, sz]
+    L.rewl_server_job_info.argtypes = [H, ll, vp, vp]
+    L.rewl_server_cancel.argtypes = [H, ll]
+    L.rewl_server_info.argtypes = [H, vp, C.POINTER(C.c_size_t)]
+    for name in ("rewl_server_create", "rewl_server_submit", "rewl_server_step", "rewl_server_poll",
+                 "rewl_server_result", "rewl_server_job_info", "rewl_server_cancel", "rewl_server_info"):
+        getattr(L, name).restype = st
+    L.rewl_server_destroy.argtypes = [H]
+    L.rewl_server_destroy.restype = None
     L.rewl_batch_destroy.argtypes = [H]
     L.rewl_batch_destroy.restype = None
     L.rewl_destroy.argtypes = [H]

@@ -219,3 +219,67 @@ class Batch:
         s = _lib.Stats()
         check(self._L.rewl_batch_stats(self._h, C.byref(s)))
         return {k: getattr(s, k) for k, _ in _lib.Stats._fields_}
+
+
+JOB_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed", 4: "cancelled"}
+
+
+class Server:
+    """Continuous batching of density-of-states jobs in a device memory pool
+    (admission by footprint, resident state, retirement on convergence)."""
+
+    def __init__(self, pool_bytes, max_jobs=256):
+        self._L = _lib.load()
+        self._h = C.c_void_p()
+        check(self._L.rewl_server_create(int(pool_bytes), max_jobs, C.byref(self._h)))
+        self._N = {}
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._L.rewl_server_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, q, L, h, overlap, m, lnf_final, flatness, exchange_interval, seed, spin_bits=0):
+        p = _lib.Params(q, L, h, overlap, m, lnf_final, flatness, exchange_interval, seed)
+        jid = C.c_longlong(0)
+        check(self._L.rewl_server_submit(self._h, C.byref(p), spin_bits, C.byref(jid)))
+        self._N[jid.value] = L * L
+        return jid.value
+
+    def step(self, rounds=4):
+        r, q = C.c_int(0), C.c_int(0)
+        check(self._L.rewl_server_step(self._h, rounds, C.byref(r), C.byref(q)))
+        return r.value, q.value
+
+    def poll(self, job):
+        st = C.c_int(0)
+        check(self._L.rewl_server_poll(self._h, job, C.byref(st)))
+        return JOB_STATES[st.value]
+
+    def result(self, job):
+        out = np.zeros(2 * self._N[job] + 1)
+        check(self._L.rewl_server_result(self._h, job, _ptr(out), out.size))
+        return out
+
+    def job_info(self, job):
+        t = np.zeros(3)
+        c = np.zeros(3, dtype=np.int64)
+        check(self._L.rewl_server_job_info(self._h, job, _ptr(t), _ptr(c)))
+        return {"t_submit": t[0], "t_admit": t[1], "t_done": t[2], "rounds": int(c[0]), "flips": int(c[1]),
+                "bytes": int(c[2])}
+
+    def cancel(self, job):
+        check(self._L.rewl_server_cancel(self._h, job))
+
+    def info(self):
+        c = np.zeros(6, dtype=np.int64)
+        f = C.c_size_t(0)
+        check(self._L.rewl_server_info(self._h, _ptr(c), C.byref(f)))
+        return {"queued": int(c[0]), "running": int(c[1]), "done": int(c[2]), "failed": int(c[3]),
+                "rounds": int(c[4]), "flips": int(c[5]), "pool_free": f.value}
