@@ -51,10 +51,12 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="potts10_L80")
+    ap.add_argument("--workload", default="potts10_L80",
+                    help="potts10_L80 (default), potts10_L20, ising_L8, batched2048 or serving")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--jobs", type=int, default=100, help="arrivals of the serving trace")
     return ap.parse_args()
 
 
@@ -305,10 +307,130 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+def run_batched(args):
+    """2048 independent instances of uneven size in one batch vs the same kind
+    of instances launched one at a time (plain form), same rounds."""
+    import numpy as np
+    import torch
+
+    from paper_1312_3004_gb300 import REWL, Batch
+    from paper_1312_3004_gb300 import workloads as WL
+
+    jobs = WL.batched_instances(2048)
+    t0 = time.perf_counter()
+    b = Batch(jobs)
+    t_create = time.perf_counter() - t0
+    stream = torch.cuda.Stream()
+    b.set_stream(stream)
+    b.run_async(args.warmup)
+    b.sync()
+    s0 = b.stats()["flips"]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.run_async(args.steps)
+    e1.record(stream)
+    b.sync()
+    ms = e0.elapsed_time(e1)
+    flips = b.stats()["flips"] - s0
+    value = flips / (ms / 1e3)
+    # plain: a sample of the instances, each alone, one after another
+    rng = np.random.default_rng(7)
+    sample = [jobs[i] for i in rng.choice(len(jobs), size=48, replace=False)]
+    p_ms, p_flips = 0.0, 0
+    for j in sample:
+        r = REWL(*WL.rewl_args(j, j["seed"]), stream=stream)
+        r.run_async(args.warmup)
+        r.sync()
+        f0 = r.stats()["flips"]
+        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r.run_async(args.steps)
+        c.record(stream)
+        r.sync()
+        p_ms += a.elapsed_time(c)
+        p_flips += r.stats()["flips"] - f0
+        r.close()
+    plain = p_flips / (p_ms / 1e3)
+    info = b.info()
+    line = {"metric": "flip attempts/s", "value": value, "unit": "flips/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "batched2048", "instances": info["instances"], "walkers": info["walkers"],
+                       "device_bytes": info["device_bytes"], "create_s": t_create,
+                       "l2": "state larger than L2 (%.0f MB)" % (info["device_bytes"] / 1e6)},
+            "plain": {"value": plain, "unit": "flips/s", "instances_sampled": len(sample),
+                      "form": "one instance per launch, instances one after another"},
+            "batched_over_plain": value / plain, "gpu_launches": 3 * args.steps}
+    print(json.dumps(line), flush=True)
+
+
+def run_serving(args):
+    """Poisson arrivals served by continuous batching vs the same jobs served
+    one at a time in arrival order (plain form: latency from a FIFO schedule of
+    the jobs' measured solo run times)."""
+    import numpy as np
+    import torch
+
+    from paper_1312_3004_gb300 import REWL, Server
+    from paper_1312_3004_gb300 import workloads as WL
+
+    trace = WL.serving_trace(n=args.jobs)
+    srv = Server(pool_bytes=2 << 30, max_jobs=512)
+    ids = []
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        now = time.perf_counter() - t0
+        while k < len(trace) and trace[k][0] <= now:
+            ids.append((srv.submit(**trace[k][1]), trace[k][0]))
+            k += 1
+        running, queued = srv.step(rounds=4)
+        if k == len(trace) and running == 0 and queued == 0:
+            break
+        if running == 0 and queued == 0 and k < len(trace):
+            time.sleep(max(0.0, min(0.01, trace[k][0] - (time.perf_counter() - t0))))
+    wall = time.perf_counter() - t0
+    lat = []
+    for jid, arrival in ids:
+        info = srv.job_info(jid)
+        lat.append(info["t_done"] - (t0 + arrival) if info["t_done"] > 0 else float("nan"))
+    lat = np.array(lat)
+    flips = srv.info()["flips"]
+    # plain: every job alone, timed, then served first-come first-served
+    solo = []
+    for _, p in trace:
+        r = REWL(*WL.rewl_args(p, p["seed"]))
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        r.run(0)
+        solo.append(time.perf_counter() - a)
+        r.close()
+    finish, plat = 0.0, []
+    for (arrival, _), d in zip(trace, solo):
+        finish = max(finish, arrival) + d
+        plat.append(finish - arrival)
+    plat = np.array(plat)
+    line = {"metric": "request latency p50/p99", "value": float(np.percentile(lat, 99)), "unit": "s (p99)",
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "throughput_flips_per_s": flips / wall, "n_gpus": 1, "higher_is_better": False,
+            "data": "synthetic", "jobs": len(trace), "arrival_rate_per_s": 50.0, "wall_s": wall,
+            "config": {"workload": "serving", "trace": "Poisson 50/s, q 2..10, L 6..12, h 2..6, m 2..4, "
+                                                       "ln f_final 1e-4/1e-5, K 2000 (trimmed to converge in seconds)"},
+            "plain": {"p50_s": float(np.percentile(plat, 50)), "p99_s": float(np.percentile(plat, 99)),
+                      "form": "each job alone, one at a time, first-come first-served",
+                      "busy_s": float(sum(solo))}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched2048":
+        run_batched(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 

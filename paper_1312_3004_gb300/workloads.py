@@ -43,3 +43,21 @@ def batched_instances(n=2048, master_seed=0x5EED0003):
                         lnf_final=1e-6, flatness=0.8, exchange_interval=10_000,
                         seed=int(rng.integers(1, 2**63))))
     return out
+
+
+def serving_trace(n=100, rate=50.0, master_seed=0x5EED0005):
+    """Poisson arrivals (exponential gaps, mean 1/rate s) of density-of-states
+    jobs, trimmed so that every job converges within seconds on one GPU:
+    q in {2..10}, L in {6..12}, h in {2..6}, m in {2..4}, ln f_final in
+    {1e-4, 1e-5}, 2000 steps between exchanges, overlap 0.75, flatness 0.8.
+    Returns [(arrival_s, params)]."""
+    rng = np.random.default_rng(master_seed)
+    t = 0.0
+    out = []
+    for _ in range(n):
+        t += float(rng.exponential(1.0 / rate))
+        out.append((t, dict(q=int(rng.integers(2, 11)), L=int(rng.integers(6, 13)), h=int(rng.integers(2, 7)),
+                            overlap=0.75, m=int(rng.integers(2, 5)),
+                            lnf_final=float(rng.choice([1e-4, 1e-5])), flatness=0.8,
+                            exchange_interval=2000, seed=int(rng.integers(1, 2**63)))))
+    return out
