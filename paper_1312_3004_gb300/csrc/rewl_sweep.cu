@@ -88,10 +88,11 @@ __device__ __forceinline__ unsigned long long u53(uint32_t hi, uint32_t lo) {
 
 // Upper bracket end that never rejects inside a window (in-window |D| < 2^62).
 constexpr long long kNoReject = 1LL << 62;
-// Shadow value of the four bins beyond each end of a window: every proposal
-// there has D >= 2^62 >= t_hi and is rejected like an out-of-window move.
+// Shadow value of the bins beyond each end of a window: every proposal there
+// has D >= 2^62 >= t_hi and is rejected like an out-of-window move.  Eight
+// bins of padding also cover the look-ahead loads of two moves of up to four.
 constexpr long long kOutside = 0x7fffffffffffffffLL;
-constexpr int kPad = 4;
+constexpr int kPad = 8;
 constexpr long long kMant = (1LL << 52) - 1, kHidden = 1LL << 52;
 
 // floor / ceil of x * 2^k as a 64-bit integer, saturating at 2^61 (x >= 0).
@@ -109,8 +110,8 @@ __device__ __forceinline__ long long scaled_ceil(float x, int k) {
 }
 
 // Bracket of T = -ln(u) / unit, unit = 2^-k: accept for sure if D < t_lo,
-// reject for sure if D >= t_hi, where D is within one unit of the true
-// difference.  uf = u with relative error <= 2^-23 (24 + 24 bits, one
+// reject for sure if D >= t_hi, where D is within three units of the true
+// difference (the shadow's floors and inexact tags, see shadow_of).  uf = u with relative error <= 2^-23 (24 + 24 bits, one
 // rounding; top >= 1 makes the 5 dropped bits <= 2^-24 relative); logf is
 // within 1 ulp; so |Lf - (-ln u)| <= (Lf + 1) 2^-22.9, and the margin
 // (Lf + 1) 2^-18 leaves a factor > 8 for that, for exp's own error (1 ulp of
@@ -125,19 +126,22 @@ __device__ __forceinline__ void accept_bracket(unsigned long long U, int k, long
     const float uf = fmaf((float)top, 0x1p-24f, (float)((uint32_t)(U >> 5) & 0xffffffu) * 0x1p-48f);
     const float Lf = -logf(uf);
     const float margin = (Lf + 1.0f) * 0x1p-18f;
-    const long long lo = scaled_floor(Lf - margin, k) - 1;
+    const long long lo = scaled_floor(Lf - margin, k) - 3;
     t_lo = lo > 0 ? lo : 0;
-    t_hi = scaled_ceil(Lf + margin, k) + 2;
+    t_hi = scaled_ceil(Lf + margin, k) + 4;
 }
 
-// floor(v / 2^(ew - 1075)) of a non-negative binary64 bit pattern v whose
-// exponent is at most ew + 10 (the result is then below 2^63).
-__device__ __forceinline__ long long fixed_floor(long long v, int ew) {
+// Shadow of a non-negative binary64 bit pattern v in half-units of
+// u = 2^(ew - 1075): 2 floor(v / u) + (1 if the floor dropped bits).  A value
+// whose tag bit is 0 is exactly (shadow / 2) u.  The exponent of v is at most
+// ew + 8, so the shadow stays below 2^62.
+__device__ __forceinline__ long long shadow_of(long long v, int ew) {
     if (v == 0) return 0;
     const int s = (int)(v >> 52) - ew;
     const long long mf = (v & kMant) | kHidden;
-    if (s >= 0) return mf << s;
-    return s <= -63 ? 0 : (mf >> -s);
+    if (s >= 0) return (mf << s) << 1;
+    if (s <= -53) return 1;
+    return ((mf >> -s) << 1) | (long long)((mf & ((1LL << -s) - 1)) != 0);
 }
 
 // v / 2^(e - 1075) for the binary64 value v = ln f if that is an integer below
@@ -218,12 +222,27 @@ struct Tally {
     unsigned int acc, seq;
 };
 
-constexpr long long kExactFloor = 1LL << 52;  // shadow values >= this are exact
-
-// Binary64 bits of the exact value F * 2^(ew - 1075), F >= 2^52.
-__device__ __forceinline__ long long from_fixed(long long F, int ew) {
+// Binary64 bits of F * 2^(ew - 1075) for an integer F >= 0 that has at most
+// 53 significant bits (a value the shadow holds exactly).
+__device__ __forceinline__ long long from_units(long long F, int ew) {
+    if (F == 0) return 0;
     const int sh = 11 - __clzll(F);  // top bit position - 52
-    return ((long long)(ew + sh) << 52) | ((F >> sh) & kMant);
+    const long long m = sh >= 0 ? (F >> sh) : (F << -sh);
+    return ((long long)(ew + sh) << 52) | (m & kMant);
+}
+
+// Round an exact shadow (tag 0) to 53 significant bits, ties to even: the
+// binary64 rounding of a ln f step that entered the next binade.
+__device__ __forceinline__ long long round_shadow(long long F2) {
+    long long F = F2 >> 1;
+    const int sh = 11 - __clzll(F);
+    if (sh <= 0) return F2;
+    const long long ulp = 1LL << sh, r = F & (ulp - 1);
+    if (r == 0) return F2;
+    const long long half = ulp >> 1;
+    F -= r;
+    if (r > half || (r == half && ((F >> sh) & 1))) F += ulp;
+    return F << 1;
 }
 
 template <int BITS, int S>
@@ -242,20 +261,22 @@ __device__ void walker_sweep(const Model &M, uint32_t *__restrict__ lat, long lo
 #pragma unroll
     for (int o = 1; o < S; o <<= 1) vmax = max(vmax, __shfl_xor_sync(gm, vmax, o));
     const double reach = __dadd_rn(__longlong_as_double(vmax), __dmul_rn((double)M.K, lnf));
-    // values stay below 2^(e_reach + 2 - 1023): below 2^62 units of 2^(ew - 1075)
-    int ew = (int)(__double_as_longlong(reach) >> 52) - 8;
+    // values stay below 2^(e_reach + 2 - 1023): below 2^61 units of
+    // u = 2^(ew - 1075), shadows (half-units) below 2^62
+    int ew = (int)(__double_as_longlong(reach) >> 52) - 7;
     if (ew < 1) ew = 1;
-    const int k = 1075 - ew;
-    for (int b = j; b < M.B; b += S) lgf[b] = fixed_floor(lgb[b], ew);
+    const int k = 1076 - ew;  // half-unit = 2^-k
+    for (int b = j; b < M.B; b += S) lgf[b] = shadow_of(lgb[b], ew);
     for (int p = j; p < kPad; p += S) {
         lgf[-1 - p] = kOutside;
         lgf[M.B + p] = kOutside;
     }
     bool addF;
-    const long long incF = exact_units(LNF, ew, addF);
+    const long long incU = exact_units(LNF, ew, addF);
+    const long long incF = incU << 1;  // ln f in half-units
     // every integer step inside a binade is exact when ln f is a multiple of the
-    // largest last place (2^10 units for values below 2^62 units)
-    const bool int_add = addF && (incF & 1023) == 0;
+    // largest last place (2^8 units for values below 2^61 units)
+    const bool int_add = addF && (incU & 255) == 0;
     if (S > 1) __syncwarp(gm);
 
     // State of the current bin: AF is its shadow, kept in lgf after every step.
@@ -303,6 +324,7 @@ __device__ void walker_sweep(const Model &M, uint32_t *__restrict__ lat, long lo
                 st.th[j] = th;
                 st.uu[j] = U;
             }
+            if (j == 0) st.a[n] = make_int4(0, 0, -1, meta_of(0, false, 0));  // look-ahead spare
             __syncwarp(gm);
             if (j < n) st.bm[site >> 5] = 0u;  // every marked word belongs to some lane's site
         } else {
@@ -311,74 +333,102 @@ __device__ void walker_sweep(const Model &M, uint32_t *__restrict__ lat, long lo
 
         // ---- serial phase: the group resolves the proposals in order ------------
         bool any_acc = false;
-        int4 an = a;
-        longlong2 tn = th;
-        if (S > 1) {
-            an = st.a[0];
-            tn = st.th[0];
-        }
-        for (int kk = 0; kk < n; ++kk) {
-            int4 ka = an;
-            const longlong2 kt = tn;
-            if (S > 1) {  // next proposal's data, one step ahead (the staging arrays are padded)
-                an = st.a[kk + 1];
-                tn = st.th[kk + 1];
+        int kk = 0;
+        while (kk < n) {
+            // ---- fast steps: integer decision and ln f step -----------------------
+            // Every step is computed speculatively; a step that needs more (a
+            // stale proposal, a draw inside the bracket, an inexact ln f step)
+            // leaves the loop before it changes anything.
+            int4 kan = S > 1 ? st.a[kk] : a;
+            longlong2 ktn = S > 1 ? st.th[kk] : th;
+            int Eo = E - lo;  // bin of the current energy in the window
+            for (; kk < n; ++kk) {
+                const int4 ka = kan;
+                const longlong2 kt = ktn;
+                if (S > 1) {  // the next proposal, one step ahead (one spare entry)
+                    kan = st.a[kk + 1];
+                    ktn = st.th[kk + 1];
+                }
+                const int kdE = (ka.w & 15) - 8;
+                const int Eno = Eo + kdE;
+                const long long BF = lgf[Eno];  // beyond the window: kOutside
+                const long long D = BF - AF;
+                const bool acc = D < kt.x;
+                const bool moved = acc && kdE != 0;
+                const long long cur = moved ? BF : AF;  // with dE = 0, BF is the current shadow
+                const long long AF2 = cur + incF;
+                // inside the bracket: t_lo <= D < t_hi, one unsigned comparison
+                const bool unsure = (unsigned long long)(D - kt.x) < (unsigned long long)(kt.y - kt.x);
+                const bool dirty = S > 1 && (ka.w & 16) && any_acc;
+                // a value with dropped bits (tag 1) takes binary64 steps
+                if (dirty || unsure || (cur & 1) || !int_add) break;
+                // a step whose top bit moves may need binary64 rounding (at
+                // 2^53 units and above the top bit is in the high word)
+                const uint32_t hc = (uint32_t)((unsigned long long)cur >> 32);
+                const uint32_t h2 = (uint32_t)((unsigned long long)AF2 >> 32);
+                long long AFn = AF2;
+                if ((h2 ^ hc) > hc) AFn = round_shadow(AF2);
+                const uint32_t word = lat[ka.x];
+                if (acc) lat[ka.x] = (word & (uint32_t)ka.z) | (uint32_t)ka.y;
+                const uint32_t hv = hg[Eo];
+                if (moved) hg[Eo] = hv + visits;
+                visits = moved ? 1u : visits + 1u;
+                Eo = moved ? Eno : Eo;
+                AF = AFn;
+                lgf[Eo] = AF;
+                any_acc |= acc;
+                nacc += acc ? 1u : 0u;
             }
-            // ---- fast step: integer decision and ln f step, one branch to check --
+            E = Eo + lo;
+            if (kk >= n) break;
+            // ---- the same step, every case done exactly ---------------------------
+            int4 ka = S > 1 ? st.a[kk] : a;
+            const longlong2 kt = S > 1 ? st.th[kk] : th;
             int kdE = (ka.w & 15) - 8;
-            int En = E + kdE;
-            long long BF = lgf[En - lo];  // beyond the window: kOutside
-            long long D = BF - AF;
-            bool acc = D < kt.x;
-            long long cur = acc ? BF : AF;
-            long long AF2 = cur + incF;
-            const bool dirty = S > 1 && (ka.w & 16) && any_acc;
-            const bool cold = dirty || (!acc && D < kt.y) || cur < kExactFloor || (AF2 ^ cur) > cur || !int_add;
-            if (cold) {
-                // ---- the same step, every case done exactly -----------------------
-                if (dirty) {  // neighbourhood changed in this batch
-                    const int per = 32 / BITS;
-                    const int ks = ka.x * per + (__ffs(~ka.z) - 1) / BITS;
-                    const int kv = (ka.w >> 8) & 0xff;
-                    const int kc = spin_get<BITS>(lat, ks);
-                    const int knw = kv + (kv >= kc);
-                    kdE = energy_change<BITS>(lat, nbrs(ks, L, N, M.divL), kc, knw);
-                    ka = proposal_word<BITS>(ks, knw);
-                    En = E + kdE;
-                    BF = lgf[En - lo];
-                    D = BF - AF;
-                    acc = D < kt.x;
-                }
-                if (!acc && D < kt.y) {  // inside the bracket (never beyond the window)
-                    tally.slow += 1;
-                    const unsigned long long kU = S > 1 ? st.uu[kk] : U;
-                    const long long Ab = AF >= kExactFloor ? from_fixed(AF, ew) : lgb[E - lo];
-                    const long long Bb = BF >= kExactFloor ? from_fixed(BF, ew) : lgb[En - lo];
-                    acc = kdE == 0 ? true : exact_accept(Ab, Bb, kU, &tally.ties);
-                }
-                cur = acc ? BF : AF;  // with dE = 0, BF is the current shadow
-                AF2 = cur + incF;
-                if (!int_add || cur < kExactFloor || (AF2 ^ cur) > cur) {  // ln g(E) += ln f in binary64
-                    tally.seq += 1;
-                    const int Eb = acc ? En : E;
-                    const long long Ab = cur >= kExactFloor ? from_fixed(cur, ew) : lgb[Eb - lo];
-                    const long long A2 = exact_add(Ab, lnf);
-                    lgb[Eb - lo] = A2;
-                    AF2 = fixed_floor(A2, ew);
-                }
+            if (S > 1 && (ka.w & 16) && any_acc) {  // neighbourhood changed in this batch
+                const int per = 32 / BITS;
+                const int ks = ka.x * per + (__ffs(~ka.z) - 1) / BITS;
+                const int kv = (ka.w >> 8) & 0xff;
+                const int kc = spin_get<BITS>(lat, ks);
+                const int knw = kv + (kv >= kc);
+                kdE = energy_change<BITS>(lat, nbrs(ks, L, N, M.divL), kc, knw);
+                ka = proposal_word<BITS>(ks, knw);
             }
-            // ---- commit (predicated stores, no branches) --------------------------
+            const int En = E + kdE;
+            const long long BF = lgf[En - lo];
+            const long long D = BF - AF;
+            bool acc = D < kt.x;
+            if (!acc && D < kt.y) {  // inside the bracket (never beyond the window)
+                tally.slow += 1;
+                const unsigned long long kU = S > 1 ? st.uu[kk] : U;
+                const long long Ab = (AF & 1) ? lgb[E - lo] : from_units(AF >> 1, ew);
+                const long long Bb = (BF & 1) ? lgb[En - lo] : from_units(BF >> 1, ew);
+                acc = kdE == 0 ? true : exact_accept(Ab, Bb, kU, &tally.ties);
+            }
+            const bool moved = acc && kdE != 0;
+            const long long cur = moved ? BF : AF;
+            long long AF2 = cur + incF;
+            if (!int_add || (cur & 1)) {  // ln g(E) += ln f in binary64
+                tally.seq += 1;
+                const int Eb = moved ? En : E;
+                const long long Ab = (cur & 1) ? lgb[Eb - lo] : from_units(cur >> 1, ew);
+                const long long A2 = exact_add(Ab, lnf);
+                lgb[Eb - lo] = A2;
+                AF2 = shadow_of(A2, ew);
+            } else {
+                AF2 = round_shadow(AF2);
+            }
             const uint32_t word = lat[ka.x];
             if (acc) lat[ka.x] = (word & (uint32_t)ka.z) | (uint32_t)ka.y;
-            const bool moved = acc && kdE != 0;
             const uint32_t hv = hg[E - lo];
             if (moved) hg[E - lo] = hv + visits;
             visits = moved ? 1u : visits + 1u;
-            E = acc ? En : E;
+            E = moved ? En : E;
             AF = AF2;
             lgf[E - lo] = AF;
             any_acc |= acc;
             nacc += acc ? 1u : 0u;
+            ++kk;
         }
         if (S > 1) __syncwarp(gm);
         t += (unsigned long long)n;
@@ -388,7 +438,7 @@ __device__ void walker_sweep(const Model &M, uint32_t *__restrict__ lat, long lo
     // the binary64 array from the authoritative shadow
     for (int b = j; b < M.B; b += S) {
         const long long F = lgf[b];
-        if (F >= kExactFloor) lgb[b] = from_fixed(F, ew);
+        if (!(F & 1)) lgb[b] = from_units(F >> 1, ew);
     }
     tally.acc += nacc;
     E_io = E;
