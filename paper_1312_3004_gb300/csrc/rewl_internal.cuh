@@ -66,7 +66,7 @@ enum : int { SWEEP_REFERENCE = 0, SWEEP_FAST = 1 };
 struct Layout {
     int stride;                   // bytes per walker (multiple of 16)
     int off_lgf, off_H, off_lat;  // byte offsets (ln g at 0)
-    int off_a, off_th, off_uu, off_bm;
+    int off_q, off_e, off_bm;     // serial-loop staging and conflict marks (lane groups)
 };
 
 // One instance of a batch, as the batched kernels see it.

@@ -196,26 +196,14 @@ __device__ __forceinline__ unsigned group_mask() {
 
 // Per-walker scratch of the lane group in shared memory (S > 1 only).
 struct Stage {
-    int4 *a;                 // [S] proposal: lattice word, new bits, keep mask, meta
-    longlong2 *th;           // [S] acceptance bracket (t_lo, t_hi)
-    unsigned long long *uu;  // [S] 53-bit uniforms (binary64 fallback only)
-    uint32_t *bm;            // [ceil(N/32)] sites touched by this batch
+    longlong2 *q;  // [S + 1] bracket of proposal k as the serial loop reads it: (t_lo, t_hi - t_lo)
+    int *e;        // [S + 1] energy change of proposal k as a byte step over the ln g shadow (8 dE)
+    uint32_t *bm;  // [ceil(N/32)] sites proposed in this batch
 };
 
-// Lattice write of one proposal as a word update: lat[w] = (lat[w] & keep) | bits.
-template <int BITS>
-__device__ __forceinline__ int4 proposal_word(int site, int nw) {
-    const int per = 32 / BITS;
-    const int sh = (site & (per - 1)) * BITS;
-    int4 a;
-    a.x = site / per;
-    a.y = (int)((uint32_t)nw << sh);
-    a.z = (int)~(((1u << BITS) - 1u) << sh);
-    a.w = 0;
-    return a;
-}
-// meta: dE + 8 in bits 0..3, maybe-dirty in bit 4, raw new-value draw v in bits 8..15
-__device__ __forceinline__ int meta_of(int dE, bool maybe, int v) { return (dE + 8) | ((maybe ? 1 : 0) << 4) | (v << 8); }
+// A bracket no difference passes: the serial loop hands the proposal to the
+// exact step (t_lo below every in-window D, width covering every D).
+constexpr long long kForceLo = -(1LL << 62);
 
 struct Tally {
     unsigned long long ties, slow;
@@ -245,6 +233,22 @@ __device__ __forceinline__ long long round_shadow(long long F2) {
     return F << 1;
 }
 
+// 64-bit shared-memory access by 32-bit shared address (the shadow array).
+__device__ __forceinline__ long long lds64(uint32_t a) {
+    long long v;
+    asm volatile("ld.shared.b64 %0, [%1];" : "=l"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ void sts64(uint32_t a, long long v) {
+    asm volatile("st.shared.b64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
+}
+
+template <int S, typename T>
+__device__ __forceinline__ T from_lane(unsigned gm, T x, int k) {
+    if (S == 1) return x;
+    return __shfl_sync(gm, x, k, S);
+}
+
 template <int BITS, int S>
 __device__ void walker_sweep(const Model &M, uint32_t *__restrict__ lat, long long *__restrict__ lgb,
                              long long *__restrict__ lgf, uint32_t *__restrict__ hg, const Stage &st, int g, int lo,
@@ -252,6 +256,7 @@ __device__ void walker_sweep(const Model &M, uint32_t *__restrict__ lat, long lo
     const int j = (int)(threadIdx.x & (unsigned)(S - 1));
     const unsigned gm = group_mask<S>();
     const int N = M.N, L = M.L;
+    constexpr int per = 32 / BITS;  // sites per lattice word
     const uint32_t qm1 = (uint32_t)(M.q - 1);
     const long long LNF = __double_as_longlong(lnf);
 
@@ -279,161 +284,179 @@ __device__ void walker_sweep(const Model &M, uint32_t *__restrict__ lat, long lo
     const bool int_add = addF && (incU & 255) == 0;
     if (S > 1) __syncwarp(gm);
 
-    // State of the current bin: AF is its shadow, kept in lgf after every step.
-    // A shadow >= 2^52 is the value exactly; below that the exact binary64 bits
-    // are kept in lgb.  Steps on such small values, ln f steps that cross a
-    // binade, and decisions inside the bracket are done in binary64.
-    int E = E_io;
-    unsigned long long t = t_io;
-    long long AF = lgf[E - lo];
-    uint32_t visits = 0;
+    // The current bin: Eo its index in the window, AF its shadow (always equal
+    // to lgf[Eo]), pcur the shared address of lgf[Eo].  A shadow >= 2^52 is the
+    // value exactly; below that the exact binary64 bits are kept in lgb.
+    int Eo = E_io - lo;
+    const uint32_t pbase = (uint32_t)__cvta_generic_to_shared(lgf);
+    long long AF = lgf[Eo];
     unsigned int nacc = 0;
 
     for (long long base = 0; base < M.K; base += S) {
         const int n = (int)((M.K - base) < S ? (M.K - base) : S);
         // ---- parallel phase: lane j prepares proposal t + j --------------------
-        int site = N + j, v = 0, nw = 0, dE = 0;
-        Site4 nb{0, 0, 0, 0};
+        int site = N + j, v = 0, dE = 0, word = 0;
+        uint32_t xr = 0;  // the flip as an xor on its lattice word
         longlong2 th = make_longlong2(0, kNoReject);
         unsigned long long U = 0;
         if (j < n) {
-            const unsigned long long tj = t + (unsigned long long)j;
+            const unsigned long long tj = t_io + (unsigned long long)j;
             const uint4 r = philox((uint32_t)tj, (uint32_t)(tj >> 32), (uint32_t)g, DOM_WL, M.key0, M.key1);
             site = (int)__umulhi(r.x, (uint32_t)N);
             v = (int)__umulhi(r.y, qm1);
             const int cur = spin_get<BITS>(lat, site);
-            nw = v + (v >= cur);
-            nb = nbrs(site, L, N, M.divL);
-            dE = energy_change<BITS>(lat, nb, cur, nw);
+            const int nw = v + (v >= cur);
+            dE = energy_change<BITS>(lat, nbrs(site, L, N, M.divL), cur, nw);
+            word = site / per;
+            xr = (uint32_t)(cur ^ nw) << ((site & (per - 1)) * BITS);
             U = u53(r.z, r.w);
             accept_bracket(U, k, th.x, th.y);
         }
-        int4 a = proposal_word<BITS>(site, nw);
+        bool flag = false;  // an earlier proposal of the batch may change dE
+        longlong2 q1 = make_longlong2(th.x, th.y - th.x);
         if (S > 1) {
             // ---- conflict marks: sites proposed in this batch -------------------
             if (j < n) atomicOr(&st.bm[site >> 5], 1u << (site & 31));
             __syncwarp(gm);
             const unsigned peers = __match_any_sync(gm, site);
             const unsigned lane = threadIdx.x & 31u;
-            bool maybe = (peers & ((1u << lane) - 1u) & gm) != 0u;
+            flag = (peers & ((1u << lane) - 1u) & gm) != 0u;
             if (j < n) {
-                maybe |= ((st.bm[nb.r >> 5] >> (nb.r & 31)) | (st.bm[nb.l >> 5] >> (nb.l & 31)) |
-                          (st.bm[nb.d >> 5] >> (nb.d & 31)) | (st.bm[nb.u >> 5] >> (nb.u & 31))) & 1u;
-                a.w = meta_of(dE, maybe, v);
-                st.a[j] = a;
-                st.th[j] = th;
-                st.uu[j] = U;
+                const Site4 nb = nbrs(site, L, N, M.divL);
+                flag |= ((st.bm[nb.r >> 5] >> (nb.r & 31)) | (st.bm[nb.l >> 5] >> (nb.l & 31)) |
+                         (st.bm[nb.d >> 5] >> (nb.d & 31)) | (st.bm[nb.u >> 5] >> (nb.u & 31))) & 1u;
+                st.q[j] = flag ? make_longlong2(kForceLo, -1LL) : q1;
+                st.e[j] = dE * 8;
             }
-            if (j == 0) st.a[n] = make_int4(0, 0, -1, meta_of(0, false, 0));  // look-ahead spare
+            if (j == 0) {  // look-ahead spare
+                st.q[n] = make_longlong2(0, 0);
+                st.e[n] = 0;
+            }
             __syncwarp(gm);
             if (j < n) st.bm[site >> 5] = 0u;  // every marked word belongs to some lane's site
-        } else {
-            a.w = meta_of(dE, false, v);
         }
 
         // ---- serial phase: the group resolves the proposals in order ------------
-        bool any_acc = false;
+        // accm: steps of the batch that accepted; done: those already written to
+        // the lattice.  The lattice and the histogram are brought up to date in
+        // parallel after the batch (and the lattice before an exact step).
+        unsigned accm = 0, done = 0;
+        const int Eb = Eo;
+        uint32_t pcur = pbase + (uint32_t)Eo * 8u;
         int kk = 0;
         while (kk < n) {
-            // ---- fast steps: integer decision and ln f step -----------------------
-            // Every step is computed speculatively; a step that needs more (a
-            // stale proposal, a draw inside the bracket, an inexact ln f step)
-            // leaves the loop before it changes anything.
-            int4 kan = S > 1 ? st.a[kk] : a;
-            longlong2 ktn = S > 1 ? st.th[kk] : th;
-            int Eo = E - lo;  // bin of the current energy in the window
-            for (; kk < n; ++kk) {
-                const int4 ka = kan;
-                const longlong2 kt = ktn;
-                if (S > 1) {  // the next proposal, one step ahead (one spare entry)
-                    kan = st.a[kk + 1];
-                    ktn = st.th[kk + 1];
+            if (int_add) {
+                // ---- fast steps: integer decision and ln f step -------------------
+                // Every step is computed speculatively; a step that needs more (a
+                // proposal whose neighbourhood may have changed, a draw inside the
+                // bracket, a value with dropped bits, a binade crossing) leaves
+                // the loop before it changes anything.
+                longlong2 qn = S > 1 ? st.q[kk] : q1;
+                int en = S > 1 ? st.e[kk] : dE * 8;
+                for (; kk < n; ++kk) {
+                    const longlong2 kq = qn;
+                    const int e8 = en;
+                    if (S > 1) {  // the next proposal, one step ahead (one spare entry)
+                        qn = st.q[kk + 1];
+                        en = st.e[kk + 1];
+                    }
+                    const uint32_t pn = pcur + (uint32_t)e8;
+                    const long long BF = lds64(pn);  // beyond the window: kOutside
+                    const long long D = BF - AF;
+                    const bool acc = D < kq.x;
+                    const bool unsure = (unsigned long long)D - (unsigned long long)kq.x < (unsigned long long)kq.y;
+                    const long long cur = acc ? BF : AF;  // with dE = 0 both are the current shadow
+                    const long long AF2 = cur + incF;
+                    const uint32_t hc = (uint32_t)((unsigned long long)cur >> 32);
+                    const uint32_t h2 = (uint32_t)((unsigned long long)AF2 >> 32);
+                    if (unsure || (cur & 1) || (h2 ^ hc) > hc) break;
+                    pcur = acc ? pn : pcur;
+                    AF = AF2;
+                    sts64(pcur, AF);
+                    accm |= acc ? (1u << kk) : 0u;
                 }
-                const int kdE = (ka.w & 15) - 8;
-                const int Eno = Eo + kdE;
-                const long long BF = lgf[Eno];  // beyond the window: kOutside
-                const long long D = BF - AF;
-                const bool acc = D < kt.x;
-                const bool moved = acc && kdE != 0;
-                const long long cur = moved ? BF : AF;  // with dE = 0, BF is the current shadow
-                const long long AF2 = cur + incF;
-                // inside the bracket: t_lo <= D < t_hi, one unsigned comparison
-                const bool unsure = (unsigned long long)(D - kt.x) < (unsigned long long)(kt.y - kt.x);
-                const bool dirty = S > 1 && (ka.w & 16) && any_acc;
-                // a value with dropped bits (tag 1) takes binary64 steps
-                if (dirty || unsure || (cur & 1) || !int_add) break;
-                // a step whose top bit moves may need binary64 rounding (at
-                // 2^53 units and above the top bit is in the high word)
-                const uint32_t hc = (uint32_t)((unsigned long long)cur >> 32);
-                const uint32_t h2 = (uint32_t)((unsigned long long)AF2 >> 32);
-                long long AFn = AF2;
-                if ((h2 ^ hc) > hc) AFn = round_shadow(AF2);
-                const uint32_t word = lat[ka.x];
-                if (acc) lat[ka.x] = (word & (uint32_t)ka.z) | (uint32_t)ka.y;
-                const uint32_t hv = hg[Eo];
-                if (moved) hg[Eo] = hv + visits;
-                visits = moved ? 1u : visits + 1u;
-                Eo = moved ? Eno : Eo;
-                AF = AFn;
-                lgf[Eo] = AF;
-                any_acc |= acc;
-                nacc += acc ? 1u : 0u;
+                Eo = (int)((pcur - pbase) >> 3);
+                if (kk >= n) break;
             }
-            E = Eo + lo;
-            if (kk >= n) break;
             // ---- the same step, every case done exactly ---------------------------
-            int4 ka = S > 1 ? st.a[kk] : a;
-            const longlong2 kt = S > 1 ? st.th[kk] : th;
-            int kdE = (ka.w & 15) - 8;
-            if (S > 1 && (ka.w & 16) && any_acc) {  // neighbourhood changed in this batch
-                const int per = 32 / BITS;
-                const int ks = ka.x * per + (__ffs(~ka.z) - 1) / BITS;
-                const int kv = (ka.w >> 8) & 0xff;
+            if (S > 1) {  // the lattice as of this step
+                if (((accm & ~done) >> j) & 1u) atomicXor(&lat[word], xr);
+                done = accm;
+                __syncwarp(gm);
+            }
+            const int ks = from_lane<S>(gm, site, kk);
+            int kdE = from_lane<S>(gm, dE, kk);
+            int kword = from_lane<S>(gm, word, kk);
+            uint32_t kxr = from_lane<S>(gm, xr, kk);
+            const long long tlo = from_lane<S>(gm, th.x, kk), thi = from_lane<S>(gm, th.y, kk);
+            if (S > 1 && from_lane<S>(gm, (int)flag, kk)) {  // recompute against the current lattice
+                const int kv = from_lane<S>(gm, v, kk);
                 const int kc = spin_get<BITS>(lat, ks);
                 const int knw = kv + (kv >= kc);
                 kdE = energy_change<BITS>(lat, nbrs(ks, L, N, M.divL), kc, knw);
-                ka = proposal_word<BITS>(ks, knw);
+                kword = ks / per;
+                kxr = (uint32_t)(kc ^ knw) << ((ks & (per - 1)) * BITS);
             }
-            const int En = E + kdE;
-            const long long BF = lgf[En - lo];
+            const int En = Eo + kdE;
+            const long long BF = lgf[En];
             const long long D = BF - AF;
-            bool acc = D < kt.x;
-            if (!acc && D < kt.y) {  // inside the bracket (never beyond the window)
+            bool acc = D < tlo;
+            if (!acc && D < thi) {  // inside the bracket (never beyond the window)
                 tally.slow += 1;
-                const unsigned long long kU = S > 1 ? st.uu[kk] : U;
-                const long long Ab = (AF & 1) ? lgb[E - lo] : from_units(AF >> 1, ew);
-                const long long Bb = (BF & 1) ? lgb[En - lo] : from_units(BF >> 1, ew);
+                const unsigned long long kU = from_lane<S>(gm, U, kk);
+                const long long Ab = (AF & 1) ? lgb[Eo] : from_units(AF >> 1, ew);
+                const long long Bb = (BF & 1) ? lgb[En] : from_units(BF >> 1, ew);
                 acc = kdE == 0 ? true : exact_accept(Ab, Bb, kU, &tally.ties);
             }
-            const bool moved = acc && kdE != 0;
-            const long long cur = moved ? BF : AF;
+            const long long cur = acc ? BF : AF;
+            const int Eb2 = acc ? En : Eo;
             long long AF2 = cur + incF;
             if (!int_add || (cur & 1)) {  // ln g(E) += ln f in binary64
                 tally.seq += 1;
-                const int Eb = moved ? En : E;
-                const long long Ab = (cur & 1) ? lgb[Eb - lo] : from_units(cur >> 1, ew);
+                const long long Ab = (cur & 1) ? lgb[Eb2] : from_units(cur >> 1, ew);
                 const long long A2 = exact_add(Ab, lnf);
-                lgb[Eb - lo] = A2;
+                lgb[Eb2] = A2;
                 AF2 = shadow_of(A2, ew);
             } else {
                 AF2 = round_shadow(AF2);
             }
-            const uint32_t word = lat[ka.x];
-            if (acc) lat[ka.x] = (word & (uint32_t)ka.z) | (uint32_t)ka.y;
-            const uint32_t hv = hg[E - lo];
-            if (moved) hg[E - lo] = hv + visits;
-            visits = moved ? 1u : visits + 1u;
-            E = moved ? En : E;
+            Eo = Eb2;
             AF = AF2;
-            lgf[E - lo] = AF;
-            any_acc |= acc;
-            nacc += acc ? 1u : 0u;
+            lgf[Eo] = AF;
+            pcur = pbase + (uint32_t)Eo * 8u;
+            if (acc) {
+                if (S == 1) lat[kword] ^= kxr;
+                else if (j == 0) atomicXor(&lat[kword], kxr);
+                accm |= 1u << kk;
+            }
+            done |= accm & (1u << kk);
+            if (j == kk) dE = kdE;  // the lane's record of its step, for the histogram
             ++kk;
         }
+
+        // ---- after the batch: lattice and histogram ----------------------------
+        if (((accm & ~done) >> j) & 1u) {
+            if (S == 1) lat[word] ^= xr;
+            else atomicXor(&lat[word], xr);
+        }
+        // the bin after step j: the batch's start plus the accepted moves up to j
+        int x = (j < n && ((accm >> j) & 1u)) ? dE : 0;
+#pragma unroll
+        for (int o = 1; o < S; o <<= 1) {
+            const int y = __shfl_up_sync(gm, x, o, S);
+            if (j >= o) x += y;
+        }
+        const int bin = j < n ? Eb + x : -1 - j;
+        if (S == 1) {
+            hg[bin] += 1u;
+        } else {
+            const unsigned same = __match_any_sync(gm, bin);
+            if (j < n && (int)(threadIdx.x & 31u) == __ffs(same) - 1) hg[bin] += (uint32_t)__popc(same);
+        }
+        nacc += (uint32_t)__popc(accm);
         if (S > 1) __syncwarp(gm);
-        t += (unsigned long long)n;
+        t_io += (unsigned long long)n;
     }
-    hg[E - lo] += visits;
     if (S > 1) __syncwarp(gm);
     // the binary64 array from the authoritative shadow
     for (int b = j; b < M.B; b += S) {
@@ -441,8 +464,7 @@ __device__ void walker_sweep(const Model &M, uint32_t *__restrict__ lat, long lo
         if (!(F & 1)) lgb[b] = from_units(F >> 1, ew);
     }
     tally.acc += nacc;
-    E_io = E;
-    t_io = t;
+    E_io = Eo + lo;
 }
 
 // P walkers g0 .. g0 + P - 1 of one instance: stage their state in shared
@@ -477,9 +499,8 @@ __device__ void sweep_block(const Model &M, const State &Sg, int g0, int P, cons
     if (grp < P && g < M.G && !Sg.done[g / M.m]) {
         unsigned char *base = smem + (size_t)grp * lay.stride;
         Stage st;
-        st.a = reinterpret_cast<int4 *>(base + lay.off_a);
-        st.th = reinterpret_cast<longlong2 *>(base + lay.off_th);
-        st.uu = reinterpret_cast<unsigned long long *>(base + lay.off_uu);
+        st.q = reinterpret_cast<longlong2 *>(base + lay.off_q);
+        st.e = reinterpret_cast<int *>(base + lay.off_e);
         st.bm = reinterpret_cast<uint32_t *>(base + lay.off_bm);
         const int w = g / M.m;
         const uint32_t c = Sg.slot_cfg[g];
@@ -556,12 +577,10 @@ Layout make_layout(const Model &M, int S) {
     l.off_lat = off;
     off += al(M.wpc * 4);
     if (S > 1) {  // one spare entry: the serial loop reads one proposal ahead
-        l.off_a = off;
+        l.off_q = off;
         off += al((S + 1) * 16);
-        l.off_th = off;
-        off += al((S + 1) * 16);
-        l.off_uu = off;
-        off += al(S * 8);
+        l.off_e = off;
+        off += al((S + 1) * 4);
         l.off_bm = off;
         off += al(((M.N + 31) / 32) * 4);
     }
