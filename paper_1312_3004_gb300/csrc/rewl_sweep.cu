@@ -89,10 +89,11 @@ __device__ __forceinline__ unsigned long long u53(uint32_t hi, uint32_t lo) {
 // Upper bracket end that never rejects inside a window (in-window |D| < 2^62).
 constexpr long long kNoReject = 1LL << 62;
 // Shadow value of the bins beyond each end of a window: every proposal there
-// has D >= 2^62 >= t_hi and is rejected like an out-of-window move.  Eight
-// bins of padding also cover the look-ahead loads of two moves of up to four.
+// has D >= 2^62 >= t_hi and is rejected like an out-of-window move.  The
+// padding also covers the loads of speculative paths (up to six moves of up
+// to four bins each, see the step tree below).
 constexpr long long kOutside = 0x7fffffffffffffffLL;
-constexpr int kPad = 8;
+constexpr int kPad = 24;
 constexpr long long kMant = (1LL << 52) - 1, kHidden = 1LL << 52;
 
 // floor / ceil of x * 2^k as a 64-bit integer, saturating at 2^61 (x >= 0).
@@ -196,10 +197,12 @@ __device__ __forceinline__ unsigned group_mask() {
 
 // Per-walker scratch of the lane group in shared memory (S > 1 only).
 struct Stage {
-    longlong2 *q;  // [S + 1] bracket of proposal k as the serial loop reads it: (t_lo, t_hi - t_lo)
-    int *e;        // [S + 1] energy change of proposal k as a byte step over the ln g shadow (8 dE)
-    uint32_t *bm;  // [ceil(N/32)] sites proposed in this batch
+    longlong2 *q;  // [S + kStagePad] bracket of proposal k as the serial loop reads it: (t_lo, t_hi - t_lo)
+    int *e;        // [S + kStagePad] energy change of proposal k as a byte step over the ln g shadow (8 dE)
+    uint32_t *bm;  // [2 nbw] sites proposed in this batch; then those proposed twice
+    int nbw;       // ceil(N / 32)
 };
+constexpr int kStagePad = 8;
 
 // A bracket no difference passes: the serial loop hands the proposal to the
 // exact step (t_lo below every in-window D, width covering every D).
@@ -241,6 +244,13 @@ __device__ __forceinline__ long long lds64(uint32_t a) {
 }
 __device__ __forceinline__ void sts64(uint32_t a, long long v) {
     asm volatile("st.shared.b64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ void sts64_if(uint32_t a, long long v, bool p) {
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q st.shared.b64 [%0], %1;\n\t}" ::"r"(a), "l"(v),
+        "r"((int)p)
+        : "memory");
 }
 
 template <int S, typename T>
@@ -291,6 +301,24 @@ __device__ void walker_sweep(const Model &M, uint32_t *__restrict__ lat, long lo
     const uint32_t pbase = (uint32_t)__cvta_generic_to_shared(lgf);
     long long AF = lgf[Eo];
     unsigned int nacc = 0;
+    // node of this lane in the step tree (lane S - 1 has none)
+    constexpr int DP = S >= 32 ? 5 : S >= 16 ? 4 : S >= 8 ? 3 : S >= 4 ? 2 : 1;
+    const int lvl = 31 - __clz(j + 1), pre = j + 1 - (1 << lvl);
+    const unsigned lane = threadIdx.x & 31u, gbase = lane & ~(unsigned)(S - 1);
+    // its ancestors, (l, pre mod 2^l) at node index 2^l - 1 + (pre mod 2^l): which
+    // they are, and the decision each must take for the path to lead here
+    unsigned anc_mask = 0u, anc_bits = 0u;
+    bool tl[DP > 1 ? DP - 1 : 1], tb[DP > 1 ? DP - 1 : 1];  // step l on the path; taken as a move
+#pragma unroll
+    for (int l = 0; l < DP - 1; ++l) {
+        tl[l] = l < lvl;
+        tb[l] = l < lvl && ((pre >> l) & 1);
+        if (l < lvl) {
+            const int a = (1 << l) - 1 + (pre & ((1 << l) - 1));
+            anc_mask |= 1u << a;
+            anc_bits |= (unsigned)((pre >> l) & 1) << a;
+        }
+    }
 
     for (long long base = 0; base < M.K; base += S) {
         const int n = (int)((M.K - base) < S ? (M.K - base) : S);
@@ -316,24 +344,29 @@ __device__ void walker_sweep(const Model &M, uint32_t *__restrict__ lat, long lo
         longlong2 q1 = make_longlong2(th.x, th.y - th.x);
         if (S > 1) {
             // ---- conflict marks: sites proposed in this batch -------------------
-            if (j < n) atomicOr(&st.bm[site >> 5], 1u << (site & 31));
+            // (a site proposed twice marks both proposals: the later one needs it)
+            const int wsite = site >> 5;
+            const uint32_t bsite = 1u << (site & 31);
+            uint32_t *dup = st.bm + st.nbw;
+            if (j < n && (atomicOr(&st.bm[wsite], bsite) & bsite)) atomicOr(&dup[wsite], bsite);
             __syncwarp(gm);
-            const unsigned peers = __match_any_sync(gm, site);
-            const unsigned lane = threadIdx.x & 31u;
-            flag = (peers & ((1u << lane) - 1u) & gm) != 0u;
             if (j < n) {
                 const Site4 nb = nbrs(site, L, N, M.divL);
-                flag |= ((st.bm[nb.r >> 5] >> (nb.r & 31)) | (st.bm[nb.l >> 5] >> (nb.l & 31)) |
-                         (st.bm[nb.d >> 5] >> (nb.d & 31)) | (st.bm[nb.u >> 5] >> (nb.u & 31))) & 1u;
+                flag = ((dup[wsite] >> (site & 31)) | (st.bm[nb.r >> 5] >> (nb.r & 31)) |
+                        (st.bm[nb.l >> 5] >> (nb.l & 31)) | (st.bm[nb.d >> 5] >> (nb.d & 31)) |
+                        (st.bm[nb.u >> 5] >> (nb.u & 31))) & 1u;
                 st.q[j] = flag ? make_longlong2(kForceLo, -1LL) : q1;
                 st.e[j] = dE * 8;
             }
-            if (j == 0) {  // look-ahead spare
-                st.q[n] = make_longlong2(0, 0);
-                st.e[n] = 0;
+            for (int p = j; p < kStagePad; p += S) {  // entries past the batch: read, never taken
+                st.q[n + p] = make_longlong2(0, 0);
+                st.e[n + p] = 0;
             }
             __syncwarp(gm);
-            if (j < n) st.bm[site >> 5] = 0u;  // every marked word belongs to some lane's site
+            if (j < n) {  // every marked word belongs to some lane's site
+                st.bm[wsite] = 0u;
+                dup[wsite] = 0u;
+            }
         }
 
         // ---- serial phase: the group resolves the proposals in order ------------
@@ -346,34 +379,114 @@ __device__ void walker_sweep(const Model &M, uint32_t *__restrict__ lat, long lo
         int kk = 0;
         while (kk < n) {
             if (int_add) {
-                // ---- fast steps: integer decision and ln f step -------------------
-                // Every step is computed speculatively; a step that needs more (a
-                // proposal whose neighbourhood may have changed, a draw inside the
-                // bracket, a value with dropped bits, a binade crossing) leaves
-                // the loop before it changes anything.
-                longlong2 qn = S > 1 ? st.q[kk] : q1;
-                int en = S > 1 ? st.e[kk] : dE * 8;
-                for (; kk < n; ++kk) {
-                    const longlong2 kq = qn;
-                    const int e8 = en;
-                    if (S > 1) {  // the next proposal, one step ahead (one spare entry)
-                        qn = st.q[kk + 1];
-                        en = st.e[kk + 1];
-                    }
-                    const uint32_t pn = pcur + (uint32_t)e8;
+                if constexpr (S == 1) {
+                    // ---- fast steps: integer decision and ln f step ---------------
+                    // The step is computed speculatively; a step that needs more (a
+                    // draw inside the bracket, a value with dropped bits, a binade
+                    // crossing) leaves the loop before it changes anything.
+                    const uint32_t pn = pcur + (uint32_t)(dE * 8);
                     const long long BF = lds64(pn);  // beyond the window: kOutside
                     const long long D = BF - AF;
-                    const bool acc = D < kq.x;
-                    const bool unsure = (unsigned long long)D - (unsigned long long)kq.x < (unsigned long long)kq.y;
+                    const bool acc = D < q1.x;
+                    const bool unsure = (unsigned long long)D - (unsigned long long)q1.x < (unsigned long long)q1.y;
                     const long long cur = acc ? BF : AF;  // with dE = 0 both are the current shadow
                     const long long AF2 = cur + incF;
                     const uint32_t hc = (uint32_t)((unsigned long long)cur >> 32);
                     const uint32_t h2 = (uint32_t)((unsigned long long)AF2 >> 32);
-                    if (unsure || (cur & 1) || (h2 ^ hc) > hc) break;
-                    pcur = acc ? pn : pcur;
-                    AF = AF2;
-                    sts64(pcur, AF);
-                    accm |= acc ? (1u << kk) : 0u;
+                    if (!(unsure || (cur & 1) || (h2 ^ hc) > hc)) {
+                        pcur = acc ? pn : pcur;
+                        AF = AF2;
+                        sts64(pcur, AF);
+                        accm |= acc ? 1u : 0u;
+                        kk = 1;
+                    }
+                } else {
+                    // ---- step tree: lane j decides node j of the tree of the next DP
+                    // steps (level lvl = the step, prefix pre = the decisions taken
+                    // before it on the way there), all from the state at the start of
+                    // the window; the ballots then follow the decisions from the
+                    // root.  A node whose step needs more (a proposal whose
+                    // neighbourhood may have changed, a draw inside the bracket, a
+                    // value with dropped bits, a binade crossing) ends the window
+                    // there, and the exact step below takes it.
+                    // the path part of a window starting at step k0 (no state needed)
+                    struct Prep {
+                        int m, oA, oB;
+                        unsigned long long incA, incB;
+                        longlong2 kq;
+                    };
+                    auto prep = [&](int k0) {
+                        Prep P;
+                        P.m = min(DP, n - k0);
+                        int e8l[DP > 1 ? DP - 1 : 1];
+#pragma unroll
+                        for (int l = 0; l < DP - 1; ++l) e8l[l] = st.e[k0 + l];
+                        const int e8i = st.e[k0 + lvl];
+                        P.kq = st.q[k0 + lvl];
+                        // bins of the path to this node, as offsets from the current one
+                        int post[DP > 1 ? DP - 1 : 1];
+                        int oA = 0;
+#pragma unroll
+                        for (int l = 0; l < DP - 1; ++l) {
+                            if (tb[l]) oA += e8l[l];
+                            post[l] = oA;  // the bin after step l (l < lvl)
+                        }
+                        P.oA = oA;
+                        P.oB = oA + e8i;
+                        // ln f steps the path has already added to the two bins
+                        int cA = 0, cB = 0;
+#pragma unroll
+                        for (int l = 0; l < DP - 1; ++l) {
+                            if (tl[l]) {
+                                cA += post[l] == P.oA ? 1 : 0;
+                                cB += post[l] == P.oB ? 1 : 0;
+                            }
+                        }
+                        P.incA = (unsigned long long)incF * (unsigned)cA;
+                        P.incB = (unsigned long long)incF * (unsigned)cB;
+                        return P;
+                    };
+                    for (;;) {
+                        const Prep P = prep(kk);
+                        const int m = P.m;
+                        const longlong2 kq = P.kq;
+                        // the node's decision (off the true path the values are
+                        // meaningless, possibly wrapped, and never used)
+                        const uint32_t pA = pcur + (uint32_t)P.oA, pB = pcur + (uint32_t)P.oB;
+                        const long long A = (long long)((unsigned long long)lds64(pA) + P.incA);
+                        const long long B = (long long)((unsigned long long)lds64(pB) + P.incB);
+                        const long long D = (long long)((unsigned long long)B - (unsigned long long)A);
+                        const bool dec = D < kq.x;
+                        const bool unsure =
+                            (unsigned long long)D - (unsigned long long)kq.x < (unsigned long long)kq.y;
+                        const long long cur = dec ? B : A;
+                        const long long A2 = (long long)((unsigned long long)cur + (unsigned long long)incF);
+                        const uint32_t hc = (uint32_t)((unsigned long long)cur >> 32);
+                        const uint32_t h2 = (uint32_t)((unsigned long long)A2 >> 32);
+                        const bool act = lvl < m;
+                        const bool bad = unsure || (cur & 1) || (h2 ^ hc) > hc;
+                        const unsigned bd = __ballot_sync(gm, act && dec) >> gbase;
+                        const unsigned bb = __ballot_sync(gm, act && bad) >> gbase;
+                        // reached: every ancestor decided as the prefix says, and cleanly
+                        const bool reached = act && (((bd ^ anc_bits) | bb) & anc_mask) == 0u;
+                        const unsigned R = __ballot_sync(gm, reached) >> gbase;  // the true path
+                        const int deep = 31 - __clz((int)R);
+                        const bool dbad = (bb >> deep) & 1u;
+                        const int c = (31 - __clz(deep + 1)) + (dbad ? 0 : 1);  // steps taken
+                        // write the ln g values of the steps taken, the latest per bin
+                        const bool commit = reached && !bad;
+                        const uint32_t pp = dec ? pB : pA;
+#pragma unroll
+                        for (int l = 0; l < DP; ++l) sts64_if(pp, A2, commit && lvl == l);  // in step order
+                        // the decisions on the true path are the deepest node's prefix
+                        const int bits = __shfl_sync(gm, (commit && dec) ? pre | (1 << lvl) : pre, deep, S);
+                        pcur = __shfl_sync(gm, bad ? pA : pp, deep, S);
+                        AF = __shfl_sync(gm, bad ? A : A2, deep, S);
+                        __syncwarp(gm);
+                        accm |= ((unsigned)bits & ((1u << c) - 1u)) << kk;
+                        kk += c;
+                        if (c < m || kk >= n) break;
+                    }
                 }
                 Eo = (int)((pcur - pbase) >> 3);
                 if (kk >= n) break;
@@ -446,12 +559,15 @@ __device__ void walker_sweep(const Model &M, uint32_t *__restrict__ lat, long lo
             const int y = __shfl_up_sync(gm, x, o, S);
             if (j >= o) x += y;
         }
-        const int bin = j < n ? Eb + x : -1 - j;
+        const int bin = Eb + x;
         if (S == 1) {
             hg[bin] += 1u;
-        } else {
-            const unsigned same = __match_any_sync(gm, bin);
-            if (j < n && (int)(threadIdx.x & 31u) == __ffs(same) - 1) hg[bin] += (uint32_t)__popc(same);
+        } else {  // one add per run of equal bins, by the run's last step
+            const int nxt = __shfl_down_sync(gm, bin, 1, S);
+            const bool last = j < n && (j == n - 1 || nxt != bin);
+            const unsigned ends = __ballot_sync(gm, last) >> gbase;
+            const unsigned below = ends & ((1u << j) - 1u);  // j < 32
+            if (last) atomicAdd(&hg[bin], (uint32_t)(j - (below ? 31 - __clz((int)below) : -1)));
         }
         nacc += (uint32_t)__popc(accm);
         if (S > 1) __syncwarp(gm);
@@ -489,7 +605,7 @@ __device__ void sweep_block(const Model &M, const State &Sg, int g0, int P, cons
         for (int i = threadIdx.x; i < M.wpc; i += blockDim.x) lat[i] = src_lat[i];
         if (S > 1) {
             uint32_t *bm = reinterpret_cast<uint32_t *>(base + lay.off_bm);
-            for (int i = threadIdx.x; i < (M.N + 31) / 32; i += blockDim.x) bm[i] = 0u;
+            for (int i = threadIdx.x; i < 2 * ((M.N + 31) / 32); i += blockDim.x) bm[i] = 0u;
         }
     }
     __syncthreads();
@@ -502,6 +618,7 @@ __device__ void sweep_block(const Model &M, const State &Sg, int g0, int P, cons
         st.q = reinterpret_cast<longlong2 *>(base + lay.off_q);
         st.e = reinterpret_cast<int *>(base + lay.off_e);
         st.bm = reinterpret_cast<uint32_t *>(base + lay.off_bm);
+        st.nbw = (M.N + 31) / 32;
         const int w = g / M.m;
         const uint32_t c = Sg.slot_cfg[g];
         int E = Sg.cfg_E[c];
@@ -576,13 +693,13 @@ Layout make_layout(const Model &M, int S) {
     off += al(M.B * 4);
     l.off_lat = off;
     off += al(M.wpc * 4);
-    if (S > 1) {  // one spare entry: the serial loop reads one proposal ahead
+    if (S > 1) {  // entries past the batch: the step tree reads up to six ahead
         l.off_q = off;
-        off += al((S + 1) * 16);
+        off += al((S + kStagePad) * 16);
         l.off_e = off;
-        off += al((S + 1) * 4);
+        off += al((S + kStagePad) * 4);
         l.off_bm = off;
-        off += al(((M.N + 31) / 32) * 4);
+        off += al(2 * ((M.N + 31) / 32) * 4);
     }
     l.stride = al(off);
     return l;
