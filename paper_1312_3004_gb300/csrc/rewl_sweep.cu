@@ -236,21 +236,13 @@ __device__ __forceinline__ long long round_shadow(long long F2) {
     return F << 1;
 }
 
-// 64-bit shared-memory access by 32-bit shared address (the shadow array).
+// 64-bit access to the shadow array by 32-bit shared address.  Lanes of a
+// group see each other's writes only across a __syncwarp.
 __device__ __forceinline__ long long lds64(uint32_t a) {
-    long long v;
-    asm volatile("ld.shared.b64 %0, [%1];" : "=l"(v) : "r"(a) : "memory");
-    return v;
+    return *reinterpret_cast<const long long *>(__cvta_shared_to_generic(a));
 }
 __device__ __forceinline__ void sts64(uint32_t a, long long v) {
-    asm volatile("st.shared.b64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
-}
-
-__device__ __forceinline__ void sts64_if(uint32_t a, long long v, bool p) {
-    asm volatile(
-        "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q st.shared.b64 [%0], %1;\n\t}" ::"r"(a), "l"(v),
-        "r"((int)p)
-        : "memory");
+    *reinterpret_cast<long long *>(__cvta_shared_to_generic(a)) = v;
 }
 
 template <int S, typename T>
@@ -261,7 +253,7 @@ __device__ __forceinline__ T from_lane(unsigned gm, T x, int k) {
 
 template <int BITS, int S>
 __device__ void walker_sweep(const Model &M, uint32_t *__restrict__ lat, long long *__restrict__ lgb,
-                             long long *__restrict__ lgf, uint32_t *__restrict__ hg, const Stage &st, int g, int lo,
+                             long long *lgf, uint32_t *__restrict__ hg, const Stage &st, int g, int lo,
                              double lnf, int &E_io, unsigned long long &t_io, Tally &tally) {
     const int j = (int)(threadIdx.x & (unsigned)(S - 1));
     const unsigned gm = group_mask<S>();
@@ -412,15 +404,16 @@ __device__ void walker_sweep(const Model &M, uint32_t *__restrict__ lat, long lo
                     // the path part of a window starting at step k0 (no state needed)
                     struct Prep {
                         int m, oA, oB;
+                        int e8[DP];  // energy changes of the window's steps (byte steps)
                         unsigned long long incA, incB;
                         longlong2 kq;
                     };
                     auto prep = [&](int k0) {
                         Prep P;
                         P.m = min(DP, n - k0);
-                        int e8l[DP > 1 ? DP - 1 : 1];
+                        int *e8l = P.e8;
 #pragma unroll
-                        for (int l = 0; l < DP - 1; ++l) e8l[l] = st.e[k0 + l];
+                        for (int l = 0; l < DP; ++l) e8l[l] = st.e[k0 + l];
                         const int e8i = st.e[k0 + lvl];
                         P.kq = st.q[k0 + lvl];
                         // bins of the path to this node, as offsets from the current one
@@ -453,8 +446,9 @@ __device__ void walker_sweep(const Model &M, uint32_t *__restrict__ lat, long lo
                         // the node's decision (off the true path the values are
                         // meaningless, possibly wrapped, and never used)
                         const uint32_t pA = pcur + (uint32_t)P.oA, pB = pcur + (uint32_t)P.oB;
-                        const long long A = (long long)((unsigned long long)lds64(pA) + P.incA);
-                        const long long B = (long long)((unsigned long long)lds64(pB) + P.incB);
+                        const long long Am = lds64(pA), Bm = lds64(pB);
+                        const long long A = (long long)((unsigned long long)Am + P.incA);
+                        const long long B = (long long)((unsigned long long)Bm + P.incB);
                         const long long D = (long long)((unsigned long long)B - (unsigned long long)A);
                         const bool dec = D < kq.x;
                         const bool unsure =
@@ -473,14 +467,18 @@ __device__ void walker_sweep(const Model &M, uint32_t *__restrict__ lat, long lo
                         const int deep = 31 - __clz((int)R);
                         const bool dbad = (bb >> deep) & 1u;
                         const int c = (31 - __clz(deep + 1)) + (dbad ? 0 : 1);  // steps taken
-                        // write the ln g values of the steps taken, the latest per bin
                         const bool commit = reached && !bad;
-                        const uint32_t pp = dec ? pB : pA;
-#pragma unroll
-                        for (int l = 0; l < DP; ++l) sts64_if(pp, A2, commit && lvl == l);  // in step order
                         // the decisions on the true path are the deepest node's prefix
                         const int bits = __shfl_sync(gm, (commit && dec) ? pre | (1 << lvl) : pre, deep, S);
-                        pcur = __shfl_sync(gm, bad ? pA : pp, deep, S);
+                        // write the ln g values of the steps taken, level by level so
+                        // that the latest value of a bin is the one that stays
+                        const uint32_t pp = dec ? pB : pA;
+#pragma unroll
+                        for (int l = 0; l < DP; ++l) {
+                            if (commit && lvl == l) sts64(pp, A2);
+                            if (l + 1 < DP) __syncwarp(gm);
+                        }
+                        pcur = __shfl_sync(gm, (bad || !dec) ? pA : pB, deep, S);
                         AF = __shfl_sync(gm, bad ? A : A2, deep, S);
                         __syncwarp(gm);
                         accm |= ((unsigned)bits & ((1u << c) - 1u)) << kk;
