@@ -316,6 +316,7 @@ __device__ void walker_sweep(const Model &M, uint32_t *__restrict__ lat, long lo
         const int n = (int)((M.K - base) < S ? (M.K - base) : S);
         // ---- parallel phase: lane j prepares proposal t + j --------------------
         int site = N + j, v = 0, dE = 0, word = 0;
+        Site4 nb{0, 0, 0, 0};
         uint32_t xr = 0;  // the flip as an xor on its lattice word
         longlong2 th = make_longlong2(0, kNoReject);
         unsigned long long U = 0;
@@ -326,7 +327,8 @@ __device__ void walker_sweep(const Model &M, uint32_t *__restrict__ lat, long lo
             v = (int)__umulhi(r.y, qm1);
             const int cur = spin_get<BITS>(lat, site);
             const int nw = v + (v >= cur);
-            dE = energy_change<BITS>(lat, nbrs(site, L, N, M.divL), cur, nw);
+            nb = nbrs(site, L, N, M.divL);
+            dE = energy_change<BITS>(lat, nb, cur, nw);
             word = site / per;
             xr = (uint32_t)(cur ^ nw) << ((site & (per - 1)) * BITS);
             U = u53(r.z, r.w);
@@ -343,7 +345,6 @@ __device__ void walker_sweep(const Model &M, uint32_t *__restrict__ lat, long lo
             if (j < n && (atomicOr(&st.bm[wsite], bsite) & bsite)) atomicOr(&dup[wsite], bsite);
             __syncwarp(gm);
             if (j < n) {
-                const Site4 nb = nbrs(site, L, N, M.divL);
                 flag = ((dup[wsite] >> (site & 31)) | (st.bm[nb.r >> 5] >> (nb.r & 31)) |
                         (st.bm[nb.l >> 5] >> (nb.l & 31)) | (st.bm[nb.d >> 5] >> (nb.d & 31)) |
                         (st.bm[nb.u >> 5] >> (nb.u & 31))) & 1u;
@@ -360,6 +361,7 @@ __device__ void walker_sweep(const Model &M, uint32_t *__restrict__ lat, long lo
                 dup[wsite] = 0u;
             }
         }
+        unsigned flagm = S > 1 ? __ballot_sync(gm, flag) >> gbase : 0u;  // the flagged steps
 
         // ---- serial phase: the group resolves the proposals in order ------------
         // accm: steps of the batch that accepted; done: those already written to
@@ -488,6 +490,26 @@ __device__ void walker_sweep(const Model &M, uint32_t *__restrict__ lat, long lo
                 }
                 Eo = (int)((pcur - pbase) >> 3);
                 if (kk >= n) break;
+            }
+            if (S > 1 && int_add && ((flagm >> kk) & 1u)) {
+                // ---- a proposal whose neighbourhood may have changed: its lane
+                // recomputes it against the lattice as of this step, and the
+                // windows go on from it
+                if (((accm & ~done) >> j) & 1u) atomicXor(&lat[word], xr);
+                done = accm;
+                __syncwarp(gm);
+                if (j == kk) {
+                    const int c0 = spin_get<BITS>(lat, site);
+                    const int nw0 = v + (v >= c0);
+                    dE = energy_change<BITS>(lat, nb, c0, nw0);
+                    xr = (uint32_t)(c0 ^ nw0) << ((site & (per - 1)) * BITS);
+                    flag = false;
+                    st.q[kk] = q1;
+                    st.e[kk] = dE * 8;
+                }
+                flagm &= ~(1u << kk);
+                __syncwarp(gm);
+                continue;
             }
             // ---- the same step, every case done exactly ---------------------------
             if (S > 1) {  // the lattice as of this step
