@@ -7,23 +7,25 @@
 //  * A group of S lanes (S = 1 .. 32, a power of two) owns one walker.  Each
 //    lane prepares one of the next S proposals in parallel: Philox block,
 //    site, new value, energy change against the lattice at the start of the
-//    batch, and an integer acceptance bracket.  The group then resolves the S
-//    proposals in order; a proposal whose neighbourhood an earlier accepted
-//    flip of the same batch touched is recomputed from the current lattice.
-//  * Fixed-point shadow of ln g: for the launch, every ln g value v of the
-//    walker is also held as F(v) = floor(v / u) with u = 2^(e_w - 1075), where
-//    e_w is nine binades below the largest value the launch can reach (so F
-//    fits in 63 bits with a binade of headroom, and |F(v) u - v| < u).  D = F(ln g(E')) - F(ln g(E)) is
-//    then within one unit of (ln g(E') - ln g(E)) / u, and the reference test
+//    batch, and an integer acceptance bracket.  Proposals whose neighbourhood
+//    another proposal of the batch touches are flagged.
+//  * Tagged fixed-point shadow of ln g: for the launch, every ln g value v of
+//    the walker is also held as F(v) = 2 floor(v / u) + (1 if the floor
+//    dropped bits), u = 2^(e_w - 1075), e_w seven binades below the largest
+//    value the launch can reach.  D = F(ln g(E')) - F(ln g(E)) is within three
+//    half-units of the true difference, and the reference test
 //    "u_rnd < exp(ln g(E) - ln g(E'))" is decided by D < T_lo (accept) or
-//    D >= T_hi (reject), with [T_lo, T_hi) bracketing -ln(u_rnd) / u with a
-//    proven margin.  Only D inside the bracket (about 1e-5 of the decisions)
-//    takes the binary64 path exp(a - b) -- the operation the reference does.
-//  * ln g(E) += ln f is an integer add on the binary64 bit pattern while the
-//    sum stays in the binade (ln f = 2^-k is then an exact multiple of the
-//    ulp), and F += ln f / u; otherwise a binary64 add and F is recomputed.
-//  * The current bin's ln g, its shadow and its visit count live in registers
-//    and are written to shared memory when the walker leaves the bin.
+//    D >= T_hi (reject), with [T_lo, T_hi) bracketing -ln(u_rnd) with a proven
+//    margin.  Only D inside the bracket (about 1e-6 of the decisions) takes
+//    the binary64 path exp(a - b) -- the operation the reference does.
+//  * ln g(E) += ln f is an integer add on the shadow (ln f = 2^-k is a whole
+//    number of half-units), rounded to 53 bits in integers when it enters the
+//    next binade; values whose shadow dropped bits take binary64 steps.
+//  * The group resolves the proposals of a batch by a tree of speculative
+//    steps: lane j decides node j of the binary tree of the next log2(S)
+//    steps from the state at the start of the window, and ballots follow the
+//    true path.  Lattice writes and the visit histogram are applied in
+//    parallel after the batch.
 #include <cstdint>
 
 #include "rewl_internal.cuh"
