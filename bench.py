@@ -67,6 +67,20 @@ def dist_env():
     return rank, world, local
 
 
+def reduce_over_ranks(dist, device, total_ms, flips, e2e_flips_per_s):
+    """Whole-job figures of independent replicas: the slowest rank's timed
+    duration, and the work (and end-to-end rate) summed over the ranks."""
+    if dist is None:
+        return total_ms, float(flips), e2e_flips_per_s
+    import torch
+
+    mx = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    sm = torch.tensor([float(flips), e2e_flips_per_s], dtype=torch.float64, device=device)
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx.item()), float(sm[0].item()), float(sm[1].item())
+
+
 # ---------------------------------------------------------------------------
 class ClockSampler:
     """nvidia-smi samples every 200 ms during the timed region."""
@@ -239,17 +253,6 @@ def run_ours(args):
     total_ms = sum(step_ms)
     flips = s1["flips"] - s0["flips"]
 
-    tot = torch.tensor([total_ms, float(flips)], dtype=torch.float64, device="cuda")
-    if dist:
-        mx = tot[:1].clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = tot[1:].clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        total_ms_max, flips_all = float(mx.item()), float(sm.item())
-    else:
-        total_ms_max, flips_all = total_ms, float(flips)
-    value = flips_all / (total_ms_max / 1e3)
-
     # end to end through the public call: rewl_run(1 round) reads the device
     # status block back into host memory every step
     e2e_steps = max(3, min(args.steps, 10))
@@ -261,12 +264,8 @@ def run_ours(args):
     e2e_s = time.perf_counter() - t0
     e2e_flips = r.stats()["flips"] - e0s
     e2e_local = e2e_flips / e2e_s
-    if dist:
-        t = torch.tensor([e2e_local], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        e2e_val = float(t.item())
-    else:
-        e2e_val = e2e_local
+    total_ms_max, flips_all, e2e_val = reduce_over_ranks(dist, "cuda", total_ms, flips, e2e_local)
+    value = flips_all / (total_ms_max / 1e3)
 
     # roofline of the dominant kernel (sweep): algorithmic lane-ops per launch
     active_walkers = flips / max(1, args.steps) / p["exchange_interval"]

@@ -70,3 +70,48 @@ def test_missing_library_fails_loudly(monkeypatch):
     monkeypatch.setattr(_lib, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         pkg.REWL(2, 8, 4, 0.75, 2, 1e-6, 0.8, 1000, 1)
+
+
+def params(**kw):
+    base = dict(q=2, L=8, h=4, overlap=0.75, m=2, lnf_final=1e-6, flatness=0.8, exchange_interval=1000, seed=1)
+    base.update(kw)
+    return _lib.Params(**base)
+
+
+def test_batch_arguments_are_checked_before_any_device_work():
+    lib = _lib.load()
+    out = C.c_void_p()
+    assert lib.rewl_batch_create(None, 1, 0, C.byref(out)) == 1
+    jobs = (_lib.Params * 2)(params(q=1), params())
+    assert lib.rewl_batch_create(jobs, 0, 0, C.byref(out)) == 1  # n < 1
+    assert lib.rewl_batch_create(jobs, 2, 0, C.byref(out)) == 1  # job 0 has q < 2
+    assert out.value is None
+    assert b"job 0" in lib.rewl_last_error()
+    wide = (_lib.Params * 1)(params(q=17))
+    assert lib.rewl_batch_create(wide, 1, 4, C.byref(out)) == 1  # q > 16 cannot pack in 4 bits
+    assert lib.rewl_batch_run(None, 1, None) == 1
+    lib.rewl_batch_destroy(None)
+
+
+def test_server_arguments_are_checked_before_any_device_work():
+    lib = _lib.load()
+    out = C.c_void_p()
+    assert lib.rewl_server_create(1024, 4, C.byref(out)) == 1  # pool below 4 KiB
+    assert lib.rewl_server_create(1 << 20, 0, C.byref(out)) == 1  # max_jobs < 1
+    assert out.value is None
+    jid = C.c_longlong()
+    p = params()
+    assert lib.rewl_server_submit(None, C.byref(p), 0, C.byref(jid)) == 1
+    assert lib.rewl_server_step(None, 1, None, None) == 1
+    lib.rewl_server_destroy(None)
+
+
+@pytest.mark.parametrize("kw", [dict(q=1), dict(L=2), dict(m=0), dict(overlap=1.0), dict(lnf_final=1.5),
+                                dict(flatness=0.0), dict(exchange_interval=0), dict(L=4, h=40)])
+def test_static_run_rejects_bad_parameters_before_any_device_work(kw):
+    lib = _lib.load()
+    p = params(**kw)
+    buf = (C.c_double * 16)()
+    conv = C.c_int(-1)
+    assert lib.rewl_run_static(C.byref(p), 0, 1, buf, None, 16, C.byref(conv), None) == 1
+    assert lib.rewl_run_static(None, 0, 1, buf, None, 16, C.byref(conv), None) == 1

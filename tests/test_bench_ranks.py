@@ -1,0 +1,67 @@
+"""The multi-rank form of bench.py (one independent replica per rank): the
+whole-job value takes the slowest rank's time and the sum of the ranks' work.
+Run as two gloo ranks on the CPU; no GPU."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+CHILD = r"""
+import json, os, sys
+sys.path.insert(0, sys.argv[1])
+import torch.distributed as dist
+import bench
+rank, world, _ = bench.dist_env()
+dist.init_process_group("gloo", init_method="env://")
+ms, flips, e2e = bench.reduce_over_ranks(dist, "cpu", 100.0 + 50.0 * rank, 1000 * (rank + 1), 7.0 + rank)
+print(json.dumps({"rank": rank, "world": world, "ms": ms, "flips": flips, "e2e": e2e}), flush=True)
+dist.destroy_process_group()
+"""
+
+
+def free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def test_two_gloo_ranks_reduce_max_time_and_summed_work():
+    pytest.importorskip("torch")
+    port = free_port()
+    procs = []
+    for rank in range(2):
+        env = dict(os.environ, RANK=str(rank), WORLD_SIZE="2", LOCAL_RANK=str(rank), MASTER_ADDR="127.0.0.1",
+                   MASTER_PORT=str(port))
+        procs.append(subprocess.Popen([sys.executable, "-c", CHILD, ROOT], env=env, stdout=subprocess.PIPE,
+                                      stderr=subprocess.PIPE, text=True))
+    outs = []
+    for p in procs:
+        out, err = p.communicate(timeout=120)
+        assert p.returncode == 0, err
+        outs.append(json.loads(out.strip().splitlines()[-1]))
+    for o in outs:
+        assert o["world"] == 2
+        assert o["ms"] == 150.0  # the slowest rank
+        assert o["flips"] == 3000.0  # 1000 + 2000
+        assert o["e2e"] == 15.0
+
+
+def test_single_rank_passes_through():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert bench.reduce_over_ranks(None, "cpu", 12.5, 40, 3.0) == (12.5, 40.0, 3.0)
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    """--impl reference under torchrun: rank 0 times the oracle, the others exit 0 without work."""
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], env=env, capture_output=True, text=True, timeout=120)
+    assert p.returncode == 0, p.stderr
+    assert p.stdout.strip() == ""
