@@ -57,6 +57,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--jobs", type=int, default=100, help="arrivals of the serving trace")
+    ap.add_argument("--converge", default="",
+                    help="comma-separated seeds: time each run to ln f < ln f_final instead of timing rounds")
+    ap.add_argument("--converge-limit", type=float, default=1800.0, help="seconds per seed before giving up")
     return ap.parse_args()
 
 
@@ -422,9 +425,52 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+def run_converge(args):
+    """Time to convergence (every window at ln f < ln f_final) of full runs,
+    one per seed: wall time of rewl_run from the created handle (set-up and
+    window entry included) until the status block reports convergence."""
+    import torch
+
+    from paper_1312_3004_gb300 import REWL
+    from paper_1312_3004_gb300 import workloads as WL
+
+    p = WL.params(args.workload)
+    seeds = [int(x) for x in args.converge.split(",") if x.strip()]
+    runs = []
+    for seed in seeds:
+        r = REWL(*WL.rewl_args(p, seed), spin_bits=p["spin_bits"])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        conv, trace, last = False, [], 0.0
+        while True:
+            conv = r.run(200)
+            el = time.perf_counter() - t0
+            if conv or el > args.converge_limit:
+                break
+            if el - last >= 30.0:
+                s = r.stats()
+                trace.append([round(el, 1), s["windows_done"], s["max_lnf"]])
+                last = el
+        s = r.stats()
+        runs.append({"seed": seed, "converged": bool(conv), "seconds": el, "rounds": s["rounds"],
+                     "flips": s["flips"], "mean_flips_per_s": s["flips"] / el, "windows_done": s["windows_done"],
+                     "progress": trace})
+        print(json.dumps({"seed_done": runs[-1]}), flush=True)
+        r.close()
+    done = [x["seconds"] for x in runs if x["converged"]]
+    line = {"metric": "time to converge", "value": statistics.median(done) if len(done) == len(runs) else None,
+            "unit": "s", "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+            "config": config_of(args.workload, p), "seeds": seeds,
+            "min_s": min(done) if done else None, "max_s": max(done) if done else None,
+            "limit_s": args.converge_limit, "runs": runs}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
-    if args.impl == "reference":
+    if args.converge:
+        run_converge(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched2048":
         run_batched(args)
