@@ -148,10 +148,15 @@ rewl_status rewl_run_phase(rewl_t h, int phase);
  *   REWL_OPT_LANES         lanes per walker of the fast sweep: 0 = chosen from
  *                          the walker count, or 1, 2, 4, 8, 16, 32
  *   REWL_OPT_WALKERS_PER_CTA  (read-only) walkers per CTA of the current plan
+ *   REWL_OPT_LATTICE       where the fast sweep keeps the lattices: set 0 =
+ *                          chosen from their size (shared memory up to 16 KB
+ *                          each), 1 = global memory (L2), 2 = shared memory;
+ *                          get: 1 if the current plan keeps them in global
+ *                          memory, else 0
  * rewl_set_option synchronises the stream and re-plans the sweep.
  * Errors: REWL_ERR_ARG (unknown option or value, or a plan that does not fit
  * in shared memory). */
-enum { REWL_OPT_SWEEP_KERNEL = 0, REWL_OPT_LANES = 1, REWL_OPT_WALKERS_PER_CTA = 2 };
+enum { REWL_OPT_SWEEP_KERNEL = 0, REWL_OPT_LANES = 1, REWL_OPT_WALKERS_PER_CTA = 2, REWL_OPT_LATTICE = 3 };
 rewl_status rewl_set_option(rewl_t h, int option, long long value);
 rewl_status rewl_get_option(rewl_t h, int option, long long *value);
 

@@ -16,7 +16,7 @@ STATUS_NAMES = {0: "REWL_OK", 1: "REWL_ERR_ARG", 2: "REWL_ERR_NOMEM", 3: "REWL_E
 
 FIELD_SPINS, FIELD_ENERGY, FIELD_REPLICA, FIELD_STEPS, FIELD_LNG, FIELD_HIST = 0, 1, 2, 3, 4, 5
 PHASE_SWEEP, PHASE_CHECK, PHASE_EXCHANGE = 0, 1, 2
-OPT_SWEEP_KERNEL, OPT_LANES, OPT_WALKERS_PER_CTA = 0, 1, 2
+OPT_SWEEP_KERNEL, OPT_LANES, OPT_WALKERS_PER_CTA, OPT_LATTICE = 0, 1, 2, 3
 FIELD_MASK, FIELD_LNF, FIELD_ITER, FIELD_DONE, FIELD_ELO, FIELD_ROUND = 6, 7, 8, 9, 10, 11
 
 

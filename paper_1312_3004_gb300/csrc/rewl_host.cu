@@ -265,7 +265,7 @@ rewl_status prepare_instance(rewl_s *h, const rewl_params &p, int spin_bits, int
     h->plan = rewl::plan_sweep(M, h->sms, (size_t)h->smem_optin, rewl::SWEEP_FAST, lanes);
     if (h->plan.P < 1)
         return fail(REWL_ERR_ARG, "one walker needs %zu bytes of shared memory (> %d)",
-                    rewl::fast_smem_per_walker(M, h->plan.lanes), h->smem_optin);
+                    rewl::fast_smem_per_walker(M, h->plan.lanes, h->plan.lat_global != 0), h->smem_optin);
     const size_t G = (size_t)M.G, B = (size_t)M.B, hh = (size_t)M.h;
     const size_t sizes[] = {G * M.wpc * 4, G * 4, G * 4, G * 8, G * B * 8, G * B * 4, hh * B, hh * 4, hh * 8, hh * 4, hh,
                             sizeof(Ctl)};
@@ -405,7 +405,7 @@ rewl_status rewl_run_phase(rewl_t h, int phase) {
 rewl_status rewl_set_option(rewl_t h, int option, long long value) {
     if (h && !h->owns) return fail(REWL_ERR_STATE, "this instance belongs to a batch: run the batch");
     if (!h) return fail(REWL_ERR_ARG, "NULL handle");
-    int kind = h->plan.kind, lanes = h->plan.lanes;
+    int kind = h->plan.kind, lanes = h->plan.lanes, lat_mode = h->lat_mode;
     if (option == REWL_OPT_SWEEP_KERNEL) {
         if (value != 0 && value != 1) return fail(REWL_ERR_ARG, "sweep kernel %lld not 0 or 1", value);
         kind = value == 0 ? rewl::SWEEP_FAST : rewl::SWEEP_REFERENCE;
@@ -414,14 +414,18 @@ rewl_status rewl_set_option(rewl_t h, int option, long long value) {
         if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8 && value != 16 && value != 32)
             return fail(REWL_ERR_ARG, "lanes per walker %lld not 0, 1, 2, 4, 8, 16 or 32", value);
         lanes = (int)value;
+    } else if (option == REWL_OPT_LATTICE) {
+        if (value < 0 || value > 2) return fail(REWL_ERR_ARG, "lattice placement %lld not 0, 1 or 2", value);
+        lat_mode = (int)value;
     } else {
         return fail(REWL_ERR_ARG, "unknown option %d", option);
     }
-    const rewl::SweepPlan plan = rewl::plan_sweep(h->M, h->sms, (size_t)h->smem_optin, kind, lanes);
+    const rewl::SweepPlan plan = rewl::plan_sweep(h->M, h->sms, (size_t)h->smem_optin, kind, lanes, lat_mode);
     if (plan.P < 1) return fail(REWL_ERR_ARG, "configuration does not fit in shared memory");
     REWL_CUDA(cudaStreamSynchronize(h->stream));
     REWL_CUDA(rewl::prepare_sweep(h->M, plan));
     h->plan = plan;
+    h->lat_mode = lat_mode;
     if (h->graph) {
         cudaGraphExecDestroy(h->graph);
         h->graph = nullptr;
@@ -434,6 +438,7 @@ rewl_status rewl_get_option(rewl_t h, int option, long long *value) {
     if (option == REWL_OPT_SWEEP_KERNEL) *value = h->plan.kind == rewl::SWEEP_FAST ? 0 : 1;
     else if (option == REWL_OPT_LANES) *value = h->plan.lanes;
     else if (option == REWL_OPT_WALKERS_PER_CTA) *value = h->plan.P;
+    else if (option == REWL_OPT_LATTICE) *value = h->plan.lat_global;
     else return fail(REWL_ERR_ARG, "unknown option %d", option);
     return REWL_OK;
 }

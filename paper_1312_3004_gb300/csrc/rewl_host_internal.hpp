@@ -20,6 +20,7 @@ struct rewl_s {
     std::vector<int32_t> e_lo;
     cudaGraphExec_t graph = nullptr;
     int sms = 0, smem_optin = 0;
+    int lat_mode = 0;  // REWL_OPT_LATTICE: 0 by size, 1 global memory, 2 shared memory
     // byte offsets of the state arrays relative to dmem (for save / load); the
     // last part is the control block
     struct Part { size_t off, bytes; };

@@ -62,11 +62,12 @@ struct State {
 
 enum : int { SWEEP_REFERENCE = 0, SWEEP_FAST = 1 };
 
-// Shared-memory layout of one walker in the fast sweep.
+// Shared-memory layout of one walker in the fast sweep.  The binary64 ln g and
+// the histogram stay in global memory (L2); off_lat < 0: so does the lattice.
 struct Layout {
-    int stride;                   // bytes per walker (multiple of 16)
-    int off_lgf, off_H, off_lat;  // byte offsets (ln g at 0)
-    int off_q, off_e, off_bm;     // serial-loop staging and conflict marks (lane groups)
+    int stride;                 // bytes per walker (multiple of 16)
+    int off_lgf, off_lat;       // byte offsets: ln g shadow (with sentinels), lattice
+    int off_q, off_e, off_bm;   // serial-loop staging and conflict marks (lane groups)
 };
 
 // One instance of a batch, as the batched kernels see it.
@@ -91,13 +92,16 @@ struct SweepPlan {
     int threads;     // CTA size
     int grid;        // CTAs
     size_t smem;     // dynamic shared memory bytes
+    int lat_global;  // fast sweep: the lattice stays in global memory (large lattices)
 };
 
 // Launchers (rewl_kernels.cu).  All enqueue on `s` and return the launch error.
 cudaError_t launch_init(const Model &M, const State &S, cudaStream_t s);
 // kind: SWEEP_REFERENCE / SWEEP_FAST; lanes: 0 = choose from the walker count.
 // A plan with P == 0 means the configuration does not fit (shared memory).
-SweepPlan plan_sweep(const Model &M, int num_sms, size_t smem_optin, int kind = SWEEP_FAST, int lanes = 0);
+// lat_mode: where the fast sweep keeps the lattices (0 by size, 1 global, 2 shared).
+SweepPlan plan_sweep(const Model &M, int num_sms, size_t smem_optin, int kind = SWEEP_FAST, int lanes = 0,
+                     int lat_mode = 0);
 cudaError_t prepare_sweep(const Model &M, const SweepPlan &p);
 cudaError_t launch_sweep(const Model &M, const State &S, const SweepPlan &p, cudaStream_t s);
 cudaError_t launch_window_check(const Model &M, const State &S, cudaStream_t s);
@@ -105,10 +109,12 @@ cudaError_t launch_exchange(const Model &M, const State &S, cudaStream_t s);
 cudaError_t launch_set_spins(const Model &M, const State &S, const uint8_t *spins_dev, cudaStream_t s);
 cudaError_t launch_get_spins(const Model &M, const State &S, uint8_t *spins_dev, cudaStream_t s);
 size_t sweep_smem_per_walker(const Model &M);
-size_t fast_smem_per_walker(const Model &M, int lanes);
+size_t fast_smem_per_walker(const Model &M, int lanes, bool lat_global = false);
 cudaError_t launch_sweep_fast(const Model &M, const State &S, const SweepPlan &p, cudaStream_t s, bool prepare);
 
-Layout fast_layout(const Model &M, int lanes);
+Layout fast_layout(const Model &M, int lanes, bool lat_global = false);
+// A lattice above this many bytes stays in global memory in the fast sweep.
+constexpr int kSharedLatticeMax = 16384;
 cudaError_t launch_batch_check(const InstDev *inst, const WinItem *wins, int n_wins, cudaStream_t s);
 cudaError_t launch_batch_exchange(const InstDev *inst, int n_inst, cudaStream_t s);
 // Persistent batched sweep for one (spin bits, lanes) class: CTAs of `threads`

@@ -456,13 +456,14 @@ size_t sweep_smem_per_walker(const Model &M) {
     return (size_t)M.B * (sizeof(double) + sizeof(uint32_t)) + (size_t)M.wpc * sizeof(uint32_t);
 }
 
-SweepPlan plan_sweep(const Model &M, int num_sms, size_t smem_optin, int kind, int lanes) {
+SweepPlan plan_sweep(const Model &M, int num_sms, size_t smem_optin, int kind, int lanes, int lat_mode) {
     SweepPlan p{};
     p.kind = kind;
     if (kind == SWEEP_FAST) {
         if (lanes <= 0) lanes = M.G <= 16 * num_sms ? 32 : (M.G <= 64 * num_sms ? 8 : 1);
         p.lanes = lanes;
-        const size_t per = fast_smem_per_walker(M, lanes);
+        p.lat_global = lat_mode == 1 ? 1 : lat_mode == 2 ? 0 : (M.wpc * 4 > kSharedLatticeMax ? 1 : 0);
+        const size_t per = fast_smem_per_walker(M, lanes, p.lat_global != 0);
         int cap = (int)(smem_optin / per);
         if (cap > 256 / lanes) cap = 256 / lanes;
         int P = (M.G + num_sms - 1) / num_sms;

@@ -201,10 +201,13 @@ __device__ __forceinline__ unsigned group_mask() {
 struct Stage {
     longlong2 *q;  // [S + kStagePad] bracket of proposal k as the serial loop reads it: (t_lo, t_hi - t_lo)
     int *e;        // [S + kStagePad] energy change of proposal k as a byte step over the ln g shadow (8 dE)
-    uint32_t *bm;  // [2 nbw] sites proposed in this batch; then those proposed twice
-    int nbw;       // ceil(N / 32)
+    uint32_t *bm;    // [2 nbw] marks of the sites proposed in this batch; then of those proposed twice
+    int nbw;         // ceil(min(N, kMarkBits) / 32)
+    uint32_t mmask;  // site -> mark: all bits when N <= kMarkBits, else kMarkBits - 1 (shared marks
+                     // only ever flag more proposals, never fewer)
 };
 constexpr int kStagePad = 8;
+constexpr int kMarkBits = 8192;
 
 // A bracket no difference passes: the serial loop hands the proposal to the
 // exact step (t_lo below every in-window D, width covering every D).
@@ -341,15 +344,17 @@ __device__ void walker_sweep(const Model &M, uint32_t *__restrict__ lat, long lo
         if (S > 1) {
             // ---- conflict marks: sites proposed in this batch -------------------
             // (a site proposed twice marks both proposals: the later one needs it)
-            const int wsite = site >> 5;
-            const uint32_t bsite = 1u << (site & 31);
+            const uint32_t ms = (uint32_t)site & st.mmask;
+            const int wsite = (int)(ms >> 5);
+            const uint32_t bsite = 1u << (ms & 31);
             uint32_t *dup = st.bm + st.nbw;
             if (j < n && (atomicOr(&st.bm[wsite], bsite) & bsite)) atomicOr(&dup[wsite], bsite);
             __syncwarp(gm);
             if (j < n) {
-                flag = ((dup[wsite] >> (site & 31)) | (st.bm[nb.r >> 5] >> (nb.r & 31)) |
-                        (st.bm[nb.l >> 5] >> (nb.l & 31)) | (st.bm[nb.d >> 5] >> (nb.d & 31)) |
-                        (st.bm[nb.u >> 5] >> (nb.u & 31))) & 1u;
+                const uint32_t mr = (uint32_t)nb.r & st.mmask, ml = (uint32_t)nb.l & st.mmask;
+                const uint32_t md = (uint32_t)nb.d & st.mmask, mu = (uint32_t)nb.u & st.mmask;
+                flag = ((dup[wsite] >> (ms & 31)) | (st.bm[mr >> 5] >> (mr & 31)) | (st.bm[ml >> 5] >> (ml & 31)) |
+                        (st.bm[md >> 5] >> (md & 31)) | (st.bm[mu >> 5] >> (mu & 31))) & 1u;
                 st.q[j] = flag ? make_longlong2(kForceLo, -1LL) : q1;
                 st.e[j] = dE * 8;
             }
@@ -605,29 +610,27 @@ __device__ void walker_sweep(const Model &M, uint32_t *__restrict__ lat, long lo
     E_io = Eo + lo;
 }
 
-// P walkers g0 .. g0 + P - 1 of one instance: stage their state in shared
-// memory, run K steps (one lane group per walker), write the state back.
-template <int BITS, int S>
+// P walkers g0 .. g0 + P - 1 of one instance: stage their lattices in shared
+// memory (LG = false; LG = true keeps large lattices in global memory), run K
+// steps (one lane group per walker), write the lattices back.  The binary64
+// ln g and the histogram of each walker stay in global memory: the launch
+// reads ln g once to build the shadow and writes it back once at the end.
+template <int BITS, int S, bool LG>
 __device__ void sweep_block(const Model &M, const State &Sg, int g0, int P, const Layout &lay, unsigned char *smem) {
     if (*(volatile unsigned int *)&Sg.ctl->all_done) return;
+    const int nbw = (min(M.N, kMarkBits) + 31) / 32;  // conflict-mark words
     for (int p = 0; p < P; ++p) {
         const int g = g0 + p;
         if (g >= M.G || Sg.done[g / M.m]) continue;
         unsigned char *base = smem + (size_t)p * lay.stride;
-        double *lg = reinterpret_cast<double *>(base);
-        uint32_t *hg = reinterpret_cast<uint32_t *>(base + lay.off_H);
-        uint32_t *lat = reinterpret_cast<uint32_t *>(base + lay.off_lat);
-        const double *src_lg = Sg.lng + (size_t)g * M.B;
-        const uint32_t *src_H = Sg.H + (size_t)g * M.B;
-        const uint32_t *src_lat = Sg.spins + (size_t)Sg.slot_cfg[g] * M.wpc;
-        for (int i = threadIdx.x; i < M.B; i += blockDim.x) {
-            lg[i] = src_lg[i];
-            hg[i] = src_H[i];
+        if (!LG) {
+            uint32_t *lat = reinterpret_cast<uint32_t *>(base + lay.off_lat);
+            const uint32_t *src_lat = Sg.spins + (size_t)Sg.slot_cfg[g] * M.wpc;
+            for (int i = threadIdx.x; i < M.wpc; i += blockDim.x) lat[i] = src_lat[i];
         }
-        for (int i = threadIdx.x; i < M.wpc; i += blockDim.x) lat[i] = src_lat[i];
         if (S > 1) {
             uint32_t *bm = reinterpret_cast<uint32_t *>(base + lay.off_bm);
-            for (int i = threadIdx.x; i < 2 * ((M.N + 31) / 32); i += blockDim.x) bm[i] = 0u;
+            for (int i = threadIdx.x; i < 2 * nbw; i += blockDim.x) bm[i] = 0u;
         }
     }
     __syncthreads();
@@ -640,15 +643,16 @@ __device__ void sweep_block(const Model &M, const State &Sg, int g0, int P, cons
         st.q = reinterpret_cast<longlong2 *>(base + lay.off_q);
         st.e = reinterpret_cast<int *>(base + lay.off_e);
         st.bm = reinterpret_cast<uint32_t *>(base + lay.off_bm);
-        st.nbw = (M.N + 31) / 32;
+        st.nbw = nbw;
+        st.mmask = M.N > kMarkBits ? (uint32_t)(kMarkBits - 1) : 0xffffffffu;
         const int w = g / M.m;
         const uint32_t c = Sg.slot_cfg[g];
         int E = Sg.cfg_E[c];
         unsigned long long t = Sg.t[g];
-        walker_sweep<BITS, S>(M, reinterpret_cast<uint32_t *>(base + lay.off_lat), reinterpret_cast<long long *>(base),
-                              reinterpret_cast<long long *>(base + lay.off_lgf) + kPad,
-                              reinterpret_cast<uint32_t *>(base + lay.off_H), st, g, Sg.e_lo[w], Sg.lnf[w], E, t,
-                              tally);
+        uint32_t *lat = LG ? Sg.spins + (size_t)c * M.wpc : reinterpret_cast<uint32_t *>(base + lay.off_lat);
+        walker_sweep<BITS, S>(M, lat, reinterpret_cast<long long *>(Sg.lng + (size_t)g * M.B),
+                              reinterpret_cast<long long *>(base + lay.off_lgf) + kPad, Sg.H + (size_t)g * M.B, st,
+                              g, Sg.e_lo[w], Sg.lnf[w], E, t, tally);
         if ((threadIdx.x & (S - 1)) == 0) {
             Sg.cfg_E[c] = E;
             Sg.t[g] = t;
@@ -661,28 +665,21 @@ __device__ void sweep_block(const Model &M, const State &Sg, int g0, int P, cons
     }
     __syncthreads();
 
-    for (int p = 0; p < P; ++p) {
-        const int gg = g0 + p;
-        if (gg >= M.G || Sg.done[gg / M.m]) continue;
-        const unsigned char *base = smem + (size_t)p * lay.stride;
-        const double *lg = reinterpret_cast<const double *>(base);
-        const uint32_t *hg = reinterpret_cast<const uint32_t *>(base + lay.off_H);
-        const uint32_t *lat = reinterpret_cast<const uint32_t *>(base + lay.off_lat);
-        double *dst_lg = Sg.lng + (size_t)gg * M.B;
-        uint32_t *dst_H = Sg.H + (size_t)gg * M.B;
-        uint32_t *dst_lat = Sg.spins + (size_t)Sg.slot_cfg[gg] * M.wpc;
-        for (int i = threadIdx.x; i < M.B; i += blockDim.x) {
-            dst_lg[i] = lg[i];
-            dst_H[i] = hg[i];
+    if (!LG) {
+        for (int p = 0; p < P; ++p) {
+            const int gg = g0 + p;
+            if (gg >= M.G || Sg.done[gg / M.m]) continue;
+            const uint32_t *lat = reinterpret_cast<const uint32_t *>(smem + (size_t)p * lay.stride + lay.off_lat);
+            uint32_t *dst_lat = Sg.spins + (size_t)Sg.slot_cfg[gg] * M.wpc;
+            for (int i = threadIdx.x; i < M.wpc; i += blockDim.x) dst_lat[i] = lat[i];
         }
-        for (int i = threadIdx.x; i < M.wpc; i += blockDim.x) dst_lat[i] = lat[i];
     }
 }
 
-template <int BITS, int S>
+template <int BITS, int S, bool LG>
 __global__ void __launch_bounds__(256) sweep_fast_kernel(Model M, State Sg, int P, Layout lay) {
     extern __shared__ __align__(16) unsigned char smem[];
-    sweep_block<BITS, S>(M, Sg, blockIdx.x * P, P, lay, smem);
+    sweep_block<BITS, S, LG>(M, Sg, blockIdx.x * P, P, lay, smem);
 }
 
 // Persistent batched sweep: each CTA takes the next item from *queue.
@@ -700,41 +697,48 @@ __global__ void __launch_bounds__(256) batch_sweep_kernel(const InstDev *inst, c
         const Model M = inst[it.inst].M;
         const State Sg = inst[it.inst].S;
         const Layout lay = inst[it.inst].lay;
-        sweep_block<BITS, S>(M, Sg, it.g0, it.P, lay, smem);
+        sweep_block<BITS, S, false>(M, Sg, it.g0, it.P, lay, smem);
         __syncthreads();
     }
 }
 
-Layout make_layout(const Model &M, int S) {
+Layout make_layout(const Model &M, int S, bool lat_global) {
     auto al = [](int x) { return (x + 15) & ~15; };
     Layout l{};
-    int off = al(M.B * 8);
+    int off = 0;
     l.off_lgf = off;
     off += al((M.B + 2 * kPad) * 8);
-    l.off_H = off;
-    off += al(M.B * 4);
-    l.off_lat = off;
-    off += al(M.wpc * 4);
+    l.off_lat = -1;
+    if (!lat_global) {
+        l.off_lat = off;
+        off += al(M.wpc * 4);
+    }
     if (S > 1) {  // entries past the batch: the step tree reads up to six ahead
         l.off_q = off;
         off += al((S + kStagePad) * 16);
         l.off_e = off;
         off += al((S + kStagePad) * 4);
         l.off_bm = off;
-        off += al(2 * ((M.N + 31) / 32) * 4);
+        off += al(2 * ((min(M.N, kMarkBits) + 31) / 32) * 4);
     }
     l.stride = al(off);
     return l;
 }
 
+template <int BITS, int S, bool LG>
+cudaError_t launch_lg(const Model &M, const State &St, const SweepPlan &p, cudaStream_t s, bool prepare) {
+    const Layout lay = make_layout(M, S, LG);
+    if (prepare)
+        return cudaFuncSetAttribute(sweep_fast_kernel<BITS, S, LG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)p.smem);
+    sweep_fast_kernel<BITS, S, LG><<<p.grid, p.threads, p.smem, s>>>(M, St, p.P, lay);
+    return cudaGetLastError();
+}
+
 template <int BITS, int S>
 cudaError_t launch_t(const Model &M, const State &St, const SweepPlan &p, cudaStream_t s, bool prepare) {
-    const Layout lay = make_layout(M, S);
-    if (prepare)
-        return cudaFuncSetAttribute(sweep_fast_kernel<BITS, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)p.smem);
-    sweep_fast_kernel<BITS, S><<<p.grid, p.threads, p.smem, s>>>(M, St, p.P, lay);
-    return cudaGetLastError();
+    return p.lat_global ? launch_lg<BITS, S, true>(M, St, p, s, prepare)
+                        : launch_lg<BITS, S, false>(M, St, p, s, prepare);
 }
 
 template <int BITS>
@@ -751,9 +755,11 @@ cudaError_t dispatch_s(const Model &M, const State &St, const SweepPlan &p, cuda
 
 }  // namespace fast
 
-size_t fast_smem_per_walker(const Model &M, int lanes) { return (size_t)fast::make_layout(M, lanes).stride; }
+size_t fast_smem_per_walker(const Model &M, int lanes, bool lat_global) {
+    return (size_t)fast::make_layout(M, lanes, lat_global).stride;
+}
 
-Layout fast_layout(const Model &M, int lanes) { return fast::make_layout(M, lanes); }
+Layout fast_layout(const Model &M, int lanes, bool lat_global) { return fast::make_layout(M, lanes, lat_global); }
 
 namespace {
 template <int BITS, int S>

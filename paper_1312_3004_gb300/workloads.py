@@ -17,6 +17,10 @@ CONFIGS = {
     # 10-state Potts L=80 (N=6400), 64 windows x 16 walkers = 1024 walkers, 4-bit spins
     "potts10_L80": dict(q=10, L=80, h=64, overlap=0.75, m=16, lnf_final=1e-8, flatness=0.8,
                         exchange_interval=10_000, spin_bits=4),
+    # The paper's own run (Sec. 3.1): 10-state Potts L=300 (N=90000), 717 windows of
+    # 1000 bins at 75% overlap, 3 walkers each (2151 walkers), 4-bit spins (45 KB lattices)
+    "potts10_L300": dict(q=10, L=300, h=717, overlap=0.75, m=3, lnf_final=1e-8, flatness=0.8,
+                         exchange_interval=10_000, spin_bits=4),
 }
 
 

@@ -102,6 +102,38 @@ def test_every_sweep_variant_matches(case, sweep):
 
 
 @pytest.mark.parametrize("lanes", [1, 8, 32])
+@pytest.mark.parametrize("case", [SMALL[0], SMALL[2], SMALL[4], SMALL[6]])
+def test_lattices_in_global_memory_match(case, lanes):
+    """The fast sweep with the lattices left in global memory (the placement
+    for large lattices, forced here at small sizes) gives the same states."""
+    from paper_1312_3004_gb300 import _lib
+    *args, sb = case
+    gpu, orc = make_pair(*args, spin_bits=sb)
+    gpu.set_option(_lib.OPT_LATTICE, 1)
+    gpu.set_option(_lib.OPT_LANES, lanes)
+    assert gpu.get_option(_lib.OPT_LATTICE) == 1
+    for n in (1, 4, 10):
+        run_both(gpu, orc, n)
+        assert_parity(gpu, orc)
+    gpu.set_option(_lib.OPT_LATTICE, 2)  # and back into shared memory mid-run
+    assert gpu.get_option(_lib.OPT_LATTICE) == 0
+    run_both(gpu, orc, 3)
+    assert_parity(gpu, orc)
+
+
+def test_large_lattices_go_to_global_memory_and_match():
+    """q=10, L=130 with 8-bit spins (16.9 KB lattices): the plan keeps them in
+    global memory, with hashed conflict marks (N > 8192); rounds against the
+    oracle."""
+    from paper_1312_3004_gb300 import _lib
+    gpu, orc = make_pair(10, 130, 8, 0.75, 1, 1e-6, 0.8, 2000, 3, spin_bits=8)
+    assert gpu.get_option(_lib.OPT_LATTICE) == 1
+    for n in (1, 2):
+        run_both(gpu, orc, n)
+        assert_parity(gpu, orc)
+
+
+@pytest.mark.parametrize("lanes", [1, 8, 32])
 def test_every_lane_width_converges_like_the_oracle(lanes):
     """Whole runs through many ln f halvings and merges (binade changes of ln g,
     exact-add fallbacks): identical final state for each lane-group width."""
