@@ -196,11 +196,19 @@ rewl_status rewl_get_stats(rewl_t h, rewl_stats *stats);
  *   REWL_FIELD_DONE   uint8  [h]       1 once ln f < lnf_final
  *   REWL_FIELD_ELO    int32  [h]       lowest energy of window i
  *   REWL_FIELD_ROUND  int64  [1]       exchange rounds completed
+ *   REWL_FIELD_TRIPS  uint32 [h*m]     by replica id c: round trips completed, i.e.
+ *                                      arrivals in window 0 after a visit to window
+ *                                      h-1 since the last stay in window 0 (checked
+ *                                      after each exchange round; 0 when h = 1)
+ *   REWL_FIELD_TRIP_END uint8 [h*m]    by replica id c: last end of the range its
+ *                                      window touched: 0 none yet, 1 window 0,
+ *                                      2 window h-1
  * bytes must equal the size above, else REWL_ERR_ARG. */
 enum {
     REWL_FIELD_SPINS = 0, REWL_FIELD_ENERGY = 1, REWL_FIELD_REPLICA = 2, REWL_FIELD_STEPS = 3,
     REWL_FIELD_LNG = 4, REWL_FIELD_HIST = 5, REWL_FIELD_MASK = 6, REWL_FIELD_LNF = 7,
-    REWL_FIELD_ITER = 8, REWL_FIELD_DONE = 9, REWL_FIELD_ELO = 10, REWL_FIELD_ROUND = 11
+    REWL_FIELD_ITER = 8, REWL_FIELD_DONE = 9, REWL_FIELD_ELO = 10, REWL_FIELD_ROUND = 11,
+    REWL_FIELD_TRIPS = 12, REWL_FIELD_TRIP_END = 13
 };
 rewl_status rewl_get_field(rewl_t h, int field, void *out, size_t bytes);
 

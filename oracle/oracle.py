@@ -57,7 +57,8 @@ def lib():
         L.orc_dims.restype = None
         for name in ("orc_get_e_lo", "orc_get_sigma", "orc_get_E", "orc_get_rep", "orc_get_t",
                      "orc_get_lng", "orc_get_H", "orc_get_mask", "orc_get_lnf", "orc_get_iter",
-                     "orc_get_done", "orc_get_xstats", "orc_set_lng", "orc_set_lnf", "orc_set_H",
+                     "orc_get_done", "orc_get_xstats", "orc_get_rt_end", "orc_get_rt_trips",
+                     "orc_set_lng", "orc_set_lnf", "orc_set_H",
                      "orc_set_mask"):
             getattr(L, name).argtypes = [vp, vp]
             getattr(L, name).restype = None
@@ -192,6 +193,8 @@ class OracleREWL:
     def iter(self): return self._get("orc_get_iter", self.h, np.int32)
     def done(self): return self._get("orc_get_done", self.h, np.uint8)
     def xstats(self): return self._get("orc_get_xstats", 2, np.uint64)
+    def rt_end(self): return self._get("orc_get_rt_end", self.G, np.uint8)
+    def rt_trips(self): return self._get("orc_get_rt_trips", self.G, np.uint32)
 
     def set_lng(self, v):
         a = np.ascontiguousarray(np.broadcast_to(v, (self.G, self.B)), dtype=np.float64)

@@ -183,6 +183,11 @@ typedef struct orc_rewl {
     double *lnf;     /* [h] ln f of window i                                  */
     int32_t *iter;   /* [h] completed WL iterations of window i              */
     uint8_t *done;   /* [h] 1 once ln f < ln f_final                          */
+    uint8_t *rt_end; /* [h*m] by replica id: last end of the energy range the
+                        replica's window touched (0 none yet, 1 lowest window,
+                        2 highest window)                                      */
+    uint32_t *rt_trips; /* [h*m] by replica id: completed round trips, lowest
+                        window -> highest -> lowest                            */
     int64_t round;   /* barriers (exchange rounds) completed                  */
     uint64_t xtried, xacc;
     int status;
@@ -195,7 +200,29 @@ void orc_destroy(orc_rewl *s)
     if (!s) return;
     free(s->e_lo); free(s->sigma); free(s->E); free(s->rep); free(s->t);
     free(s->lng); free(s->H); free(s->mask); free(s->lnf); free(s->iter); free(s->done);
+    free(s->rt_end); free(s->rt_trips);
     free(s);
+}
+
+/* Replica diffusion through the windows (the quantity REWL's exchanges are
+ * there to speed up, Sec. 2): after every exchange round, a replica held by a
+ * walker of the lowest window completes a round trip if it has been in the
+ * highest window since it last was in the lowest one.  With one window there
+ * are no round trips.  Replica c is held by walker g when rep[g] = c. */
+void orc_track_round_trips(orc_rewl *s)
+{
+    size_t G = (size_t)s->h * s->m;
+    if (s->h < 2) return;
+    for (size_t g = 0; g < G; ++g) {
+        uint32_t c = s->rep[g];
+        int w = (int)(g / (size_t)s->m);
+        if (w == 0) {
+            if (s->rt_end[c] == 2) s->rt_trips[c] += 1;
+            s->rt_end[c] = 1;
+        } else if (w == s->h - 1) {
+            s->rt_end[c] = 2;
+        }
+    }
 }
 
 /* Start of the run (Sec. 3.2 describes the same set-up: each walker is handed a
@@ -266,8 +293,10 @@ orc_rewl *orc_create(int q, int L, int h, double overlap, int m, double lnf_fina
     s->lnf = calloc((size_t)h, sizeof(double));
     s->iter = calloc((size_t)h, sizeof(int32_t));
     s->done = calloc((size_t)h, 1);
+    s->rt_end = calloc(G, 1);
+    s->rt_trips = calloc(G, sizeof(uint32_t));
     if (!s->e_lo || !s->sigma || !s->E || !s->rep || !s->t || !s->lng || !s->H || !s->mask ||
-        !s->lnf || !s->iter || !s->done) {
+        !s->lnf || !s->iter || !s->done || !s->rt_end || !s->rt_trips) {
         orc_destroy(s);
         return NULL;
     }
@@ -282,6 +311,7 @@ orc_rewl *orc_create(int q, int L, int h, double overlap, int m, double lnf_fina
             return NULL;
         }
     }
+    orc_track_round_trips(s); /* the replicas' starting windows */
     *status = ORC_OK;
     return s;
 }
@@ -464,6 +494,7 @@ int orc_barrier(orc_rewl *s)
     orc_update_mask(s);
     orc_window_iterations(s);
     orc_exchange(s);
+    orc_track_round_trips(s);
     s->round += 1;
     return ORC_OK;
 }
@@ -612,6 +643,11 @@ void orc_get_lnf(const orc_rewl *s, double *o) { memcpy(o, s->lnf, sizeof(double
 void orc_get_iter(const orc_rewl *s, int32_t *o) { memcpy(o, s->iter, sizeof(int32_t) * (size_t)s->h); }
 void orc_get_done(const orc_rewl *s, uint8_t *o) { memcpy(o, s->done, (size_t)s->h); }
 void orc_get_xstats(const orc_rewl *s, uint64_t o[2]) { o[0] = s->xtried; o[1] = s->xacc; }
+void orc_get_rt_end(const orc_rewl *s, uint8_t *o) { memcpy(o, s->rt_end, (size_t)s->h * s->m); }
+void orc_get_rt_trips(const orc_rewl *s, uint32_t *o)
+{
+    memcpy(o, s->rt_trips, sizeof(uint32_t) * (size_t)s->h * s->m);
+}
 
 void orc_set_lng(orc_rewl *s, const double *v)
 {

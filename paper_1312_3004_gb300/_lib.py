@@ -18,6 +18,7 @@ FIELD_SPINS, FIELD_ENERGY, FIELD_REPLICA, FIELD_STEPS, FIELD_LNG, FIELD_HIST = 0
 PHASE_SWEEP, PHASE_CHECK, PHASE_EXCHANGE = 0, 1, 2
 OPT_SWEEP_KERNEL, OPT_LANES, OPT_WALKERS_PER_CTA, OPT_LATTICE = 0, 1, 2, 3
 FIELD_MASK, FIELD_LNF, FIELD_ITER, FIELD_DONE, FIELD_ELO, FIELD_ROUND = 6, 7, 8, 9, 10, 11
+FIELD_TRIPS, FIELD_TRIP_END = 12, 13
 
 
 class RewlError(RuntimeError):

@@ -268,7 +268,7 @@ rewl_status prepare_instance(rewl_s *h, const rewl_params &p, int spin_bits, int
                     rewl::fast_smem_per_walker(M, h->plan.lanes, h->plan.lat_global != 0), h->smem_optin);
     const size_t G = (size_t)M.G, B = (size_t)M.B, hh = (size_t)M.h;
     const size_t sizes[] = {G * M.wpc * 4, G * 4, G * 4, G * 8, G * B * 8, G * B * 4, hh * B, hh * 4, hh * 8, hh * 4, hh,
-                            sizeof(Ctl)};
+                            G, G * 4, sizeof(Ctl)};
     size_t off = 0;
     h->parts.clear();
     for (size_t sz : sizes) {
@@ -294,7 +294,9 @@ void carve_instance(rewl_s *h, void *base) {
     S.lnf = (double *)at(8);
     S.iter = (int32_t *)at(9);
     S.done = (uint8_t *)at(10);
-    S.ctl = (Ctl *)at(11);
+    S.rt_end = (uint8_t *)at(11);
+    S.rt_trips = (uint32_t *)at(12);
+    S.ctl = (Ctl *)at(13);
 }
 
 cudaError_t init_instance_async(rewl_s *h, cudaStream_t s) {
@@ -548,6 +550,8 @@ static rewl_status field_geometry(rewl_t h, int field, void **dev, size_t *bytes
     case REWL_FIELD_DONE: *dev = h->S.done; *bytes = hh; break;
     case REWL_FIELD_ELO: *dev = h->S.e_lo; *bytes = hh * 4; break;
     case REWL_FIELD_ROUND: *dev = &h->S.ctl->round; *bytes = 8; break;
+    case REWL_FIELD_TRIPS: *dev = h->S.rt_trips; *bytes = G * 4; break;
+    case REWL_FIELD_TRIP_END: *dev = h->S.rt_end; *bytes = G; break;
     default: return fail(REWL_ERR_ARG, "unknown field %d", field);
     }
     return REWL_OK;

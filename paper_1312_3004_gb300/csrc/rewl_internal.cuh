@@ -57,6 +57,8 @@ struct State {
     double *lnf;          // [h] ln f of each window
     int32_t *iter;        // [h] completed iterations
     uint8_t *done;        // [h] window finished
+    uint8_t *rt_end;      // [G] by replica id: last end of the energy range its window touched (0, 1 low, 2 high)
+    uint32_t *rt_trips;   // [G] by replica id: completed round trips (lowest window -> highest -> lowest)
     Ctl *ctl;             // control block
 };
 

@@ -137,6 +137,10 @@ __global__ void init_kernel(Model M, State S) {
     }
     S.cfg_E[g] = E;
     S.slot_cfg[g] = (uint32_t)g;
+    // replica g starts in walker g's window
+    const int wg = g / M.m;
+    S.rt_end[g] = M.h < 2 ? 0 : (wg == 0 ? 1 : (wg == M.h - 1 ? 2 : 0));
+    S.rt_trips[g] = 0u;
     S.t[g] = 0ull;
 }
 
@@ -393,6 +397,20 @@ __device__ void exchange_block(const Model &M, const State &S) {
     if (tried) atomicAdd(&ctl->xtried, tried);
     if (acc) atomicAdd(&ctl->xacc, acc);
     __syncthreads();
+    // replica round trips: a replica now in the lowest window completes one if
+    // it has been in the highest window since it last was in the lowest
+    if (M.h >= 2) {
+        for (int g = threadIdx.x; g < M.G; g += blockDim.x) {
+            const uint32_t c = S.slot_cfg[g];
+            const int w = g / m;
+            if (w == 0) {
+                if (S.rt_end[c] == 2) S.rt_trips[c] += 1u;
+                S.rt_end[c] = 1;
+            } else if (w == M.h - 1) {
+                S.rt_end[c] = 2;
+            }
+        }
+    }
     if (threadIdx.x == 0) {
         ctl->round = round + 1ull;
         unsigned int all = 1u;

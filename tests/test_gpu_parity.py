@@ -26,7 +26,8 @@ def make_pair(q, L, h, o, m, lnf_final, flat, K, seed, spin_bits=0):
 def differences(gpu, orc):
     diff = []
     pairs = [("spins", orc.sigma()), ("energy", orc.E()), ("replica", orc.rep()), ("steps", orc.t()),
-             ("hist", orc.H()), ("mask", orc.mask()), ("iter", orc.iter()), ("done", orc.done())]
+             ("hist", orc.H()), ("mask", orc.mask()), ("iter", orc.iter()), ("done", orc.done()),
+             ("trips", orc.rt_trips()), ("trip_end", orc.rt_end())]
     for name, want in pairs:
         got = gpu.get(name)
         if not np.array_equal(got, want):

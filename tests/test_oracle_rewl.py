@@ -377,3 +377,52 @@ def test_runs_are_deterministic_in_the_seed():
         r.run(20)
     assert np.array_equal(a.lng(), b.lng()) and np.array_equal(a.sigma(), b.sigma())
     assert not np.array_equal(a.lng(), c.lng())
+
+
+def round_trips_from_windows(history, h):
+    """Round trips re-derived from the window of every replica after each
+    round: an arrival in window 0 after a visit to window h-1 since the last
+    stay in window 0."""
+    n = history.shape[1]
+    trips = np.zeros(n, dtype=np.int64)
+    end = np.zeros(n, dtype=np.int64)
+    for windows in history:
+        for c in range(n):
+            if windows[c] == 0:
+                if end[c] == 2:
+                    trips[c] += 1
+                end[c] = 1
+            elif windows[c] == h - 1:
+                end[c] = 2
+    return trips, end
+
+
+@pytest.mark.parametrize("h,m,K,seed", [(3, 2, 300, 1), (4, 3, 200, 2), (2, 4, 150, 3)])
+def test_round_trips_follow_the_replicas_path(h, m, K, seed):
+    """The replica round-trip counters equal a count re-derived from each
+    replica's window round by round (window of replica c = window of the
+    walker g with rep[g] = c)."""
+    o = O.OracleREWL(2, 6, h, 0.75, m, 1e-4, 0.8, K, seed)
+    hist = []
+
+    def windows():
+        rep = o.rep()
+        w = np.empty(len(rep), dtype=np.int64)
+        w[rep] = np.arange(len(rep)) // m
+        return w
+
+    hist.append(windows())
+    for _ in range(60):
+        if o.run(1):
+            break
+        hist.append(windows())
+    trips, end = round_trips_from_windows(np.array(hist), h)
+    assert np.array_equal(o.rt_trips(), trips)
+    assert np.array_equal(o.rt_end(), end)
+    assert trips.sum() > 0  # replicas do travel through all the windows here
+
+
+def test_one_window_has_no_round_trips():
+    o = O.OracleREWL(2, 6, 1, 0.75, 3, 1e-3, 0.8, 300, 4)
+    o.run(10)
+    assert not o.rt_trips().any() and not o.rt_end().any()
