@@ -61,6 +61,9 @@ def parse_args():
     ap.add_argument("--converge", default="",
                     help="comma-separated seeds: time each run to ln f < ln f_final instead of timing rounds")
     ap.add_argument("--converge-limit", type=float, default=1800.0, help="seconds per seed before giving up")
+    ap.add_argument("--concurrent", action="store_true",
+                    help="with --converge: run the seeds at the same time, one stream each (for small "
+                         "workloads that leave most SMs idle)")
     return ap.parse_args()
 
 
@@ -443,7 +446,29 @@ def run_converge(args):
     p = WL.params(args.workload)
     seeds = [int(x) for x in args.converge.split(",") if x.strip()]
     runs = []
-    for seed in seeds:
+    if args.concurrent:
+        hs = [(seed, REWL(*WL.rewl_args(p, seed), spin_bits=p["spin_bits"], stream=torch.cuda.Stream()))
+              for seed in seeds]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        finish = {}
+        el = 0.0
+        while len(finish) < len(hs) and el < args.converge_limit:
+            for seed, r in hs:
+                if seed not in finish:
+                    r.run_async(50)
+            for seed, r in hs:
+                if seed not in finish and r.sync():
+                    finish[seed] = time.perf_counter() - t0
+            el = time.perf_counter() - t0
+        for seed, r in hs:
+            s = r.stats()
+            secs = finish.get(seed, el)
+            runs.append({"seed": seed, "converged": seed in finish, "seconds": secs, "rounds": s["rounds"],
+                         "flips": s["flips"], "mean_flips_per_s": s["flips"] / secs,
+                         "windows_done": s["windows_done"], "progress": []})
+            r.close()
+    for seed in ([] if args.concurrent else seeds):
         r = REWL(*WL.rewl_args(p, seed), spin_bits=p["spin_bits"])
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -468,7 +493,7 @@ def run_converge(args):
             "unit": "s", "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
             "config": config_of(args.workload, p), "seeds": seeds,
             "min_s": min(done) if done else None, "max_s": max(done) if done else None,
-            "limit_s": args.converge_limit, "runs": runs}
+            "limit_s": args.converge_limit, "concurrent": bool(args.concurrent), "runs": runs}
     print(json.dumps(line), flush=True)
 
 
