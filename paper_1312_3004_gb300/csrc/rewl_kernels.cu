@@ -1,8 +1,11 @@
 // rewl_kernels.cu -- sm_103a kernels of the REWL hot path (arXiv:1312.3004, Sec. 2):
 //   init_kernel         initial configuration + entry into the walker's window
-//   sweep_kernel        K Wang-Landau steps per walker (the hot loop)
+//   sweep_kernel        K Wang-Landau steps per walker, binary64 on the walker's
+//                       chain (the reference sweep; the production sweep is the
+//                       fast sweep of rewl_sweep.cu, which reaches the same states)
 //   window_check_kernel visited mask, flatness, merge of ln g, f -> sqrt f
-//   exchange_kernel     replica exchange between neighbouring windows (Eq. 1)
+//   exchange_kernel     replica exchange between neighbouring windows (Eq. 1),
+//                       then the replicas' round-trip counters
 //
 // Arithmetic contract (shared with the CPU oracle, written independently):
 // spins, energies, histograms and random words are integers; ln g, the

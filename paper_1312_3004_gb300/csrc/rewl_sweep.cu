@@ -410,7 +410,8 @@ __device__ void walker_sweep(const Model &M, uint32_t *__restrict__ lat, long lo
                     // neighbourhood may have changed, a draw inside the bracket, a
                     // value with dropped bits, a binade crossing) ends the window
                     // there, and the exact step below takes it.
-                    // the path part of a window starting at step k0 (no state needed)
+                    //
+                    // The path part of a window starting at step k0 needs no state.
                     struct Prep {
                         int m, oA, oB;
                         int e8[DP];  // energy changes of the window's steps (byte steps)
