@@ -294,7 +294,12 @@ def run_ours(args):
                      "frac": achieved / peak, "traffic": None,
                      "kernel": "sweep_kernel", "avg_launch_ms": sweep_avg_s * 1e3,
                      "ops_per_flip": ALG_OPS_PER_FLIP,
-                     "peak_basis": "152 SMs x 128 INT32/FP32 lanes x 2070 MHz (recipe unit counts)"},
+                     "peak_basis": "152 SMs x 128 INT32/FP32 lanes x 2070 MHz (recipe unit counts)",
+                     # each walker's steps form one dependent chain: the clock cycles
+                     # one step of one walker takes (walkers x clock / flips per second)
+                     "chain_cycles_per_step": (active_walkers * (clocks.get("sm_mhz") or SM_MAX_MHZ) * 1e6
+                                               / (value / world)) if value > 0 else None,
+                     "walkers": active_walkers},
         "e2e": {"value": e2e_val, "unit": "flips/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 64,
                 "call": "rewl_run(handle, 1 round) incl. status read-back", "steps": e2e_steps},
         "gpu_launches": 3 * args.steps,
