@@ -334,22 +334,29 @@ def run_batched(args):
     from paper_1312_3004_gb300 import workloads as WL
 
     jobs = WL.batched_instances(2048)
-    t0 = time.perf_counter()
-    b = Batch(jobs)
-    t_create = time.perf_counter() - t0
     stream = torch.cuda.Stream()
-    b.set_stream(stream)
-    b.run_async(args.warmup)
-    b.sync()
-    s0 = b.stats()["flips"]
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    b.run_async(args.steps)
-    e1.record(stream)
-    b.sync()
-    ms = e0.elapsed_time(e1)
-    flips = b.stats()["flips"] - s0
+
+    def timed_batch(lanes):
+        t0 = time.perf_counter()
+        bb = Batch(jobs, lanes=lanes)
+        tc = time.perf_counter() - t0
+        bb.set_stream(stream)
+        bb.run_async(args.warmup)
+        bb.sync()
+        f0 = bb.stats()["flips"]
+        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        bb.run_async(args.steps)
+        c.record(stream)
+        bb.sync()
+        return bb, tc, a.elapsed_time(c), bb.stats()["flips"] - f0
+
+    # the chosen mapping (a thread per walker at this walker count) and the other one
+    b, t_create, ms, flips = timed_batch(0)
     value = flips / (ms / 1e3)
+    b32, _, ms32, flips32 = timed_batch(32)
+    groups = flips32 / (ms32 / 1e3)
+    b32.close()
     # plain: a sample of the instances, each alone, one after another
     rng = np.random.default_rng(7)
     sample = [jobs[i] for i in rng.choice(len(jobs), size=48, replace=False)]
@@ -377,7 +384,10 @@ def run_batched(args):
                        "l2": "state larger than L2 (%.0f MB)" % (info["device_bytes"] / 1e6)},
             "plain": {"value": plain, "unit": "flips/s", "instances_sampled": len(sample),
                       "form": "one instance per launch, instances one after another"},
-            "batched_over_plain": value / plain, "gpu_launches": 3 * args.steps}
+            "batched_over_plain": value / plain, "gpu_launches": 3 * args.steps,
+            "mapping": "thread per walker, state in global memory",
+            "lane_groups": {"value": groups, "unit": "flips/s",
+                            "form": "32 lanes per walker, state staged in shared memory"}}
     print(json.dumps(line), flush=True)
 
 

@@ -240,6 +240,13 @@ typedef struct rewl_batch_s *rewl_batch_t;
 /* Create a batch of n instances (jobs[i] as in rewl_create; spin_bits as in
  * rewl_create_ext, applied to all).  Errors as rewl_create, naming the job. */
 rewl_status rewl_batch_create(const rewl_params *jobs, int n, int spin_bits, rewl_batch_t *out);
+/* As rewl_batch_create, choosing how walkers map to threads: lanes = 32, a
+ * group of 32 lanes per walker with its state staged in shared memory (walker
+ * groups of one instance per CTA); lanes = 1, a thread per walker with all its
+ * state in global memory (walkers of any instances in a CTA); lanes = 0,
+ * chosen from the total walker count (1 from 16384 walkers on).  Results are
+ * the same either way.  Errors: REWL_ERR_ARG for another lanes value. */
+rewl_status rewl_batch_create_ext(const rewl_params *jobs, int n, int spin_bits, int lanes, rewl_batch_t *out);
 
 /* Run rounds of every unfinished instance until all have converged or
  * max_rounds rounds were queued (<= 0: no limit); synchronises.

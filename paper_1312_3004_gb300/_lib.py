@@ -84,6 +84,7 @@ def load():
     L.rewl_run_static.argtypes = [C.POINTER(Params), i32, ll, vp, vp, sz, C.POINTER(C.c_int), vp]
     L.rewl_run_static.restype = st
     L.rewl_batch_create.argtypes = [C.POINTER(Params), i32, i32, C.POINTER(H)]
+    L.rewl_batch_create_ext.argtypes = [C.POINTER(Params), i32, i32, i32, C.POINTER(H)]
     L.rewl_batch_run.argtypes = [H, ll, C.POINTER(C.c_int)]
     L.rewl_batch_run_async.argtypes = [H, ll]
     L.rewl_batch_sync.argtypes = [H, C.POINTER(C.c_int)]
@@ -91,7 +92,7 @@ def load():
     L.rewl_batch_instance.argtypes = [H, i32, C.POINTER(H)]
     L.rewl_batch_info.argtypes = [H, C.POINTER(C.c_int), C.POINTER(C.c_longlong), C.POINTER(C.c_size_t)]
     L.rewl_batch_stats.argtypes = [H, C.POINTER(Stats)]
-    for name in ("rewl_batch_create", "rewl_batch_run", "rewl_batch_run_async", "rewl_batch_sync",
+    for name in ("rewl_batch_create", "rewl_batch_create_ext", "rewl_batch_run", "rewl_batch_run_async", "rewl_batch_sync",
                  "rewl_batch_set_stream", "rewl_batch_instance", "rewl_batch_info", "rewl_batch_stats"):
         getattr(L, name).restype = st
     L.rewl_server_create.argtypes = [sz, i32, C.POINTER(H)]

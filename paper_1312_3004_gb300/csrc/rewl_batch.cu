@@ -32,10 +32,15 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 struct SweepClass {
     int bits = 4, lanes = 32, threads = 0, grid = 0;
     size_t smem = 0;
-    std::vector<rewl::SweepItem> items;
+    std::vector<rewl::SweepItem> items;      // lanes 32: groups of walkers of one instance
     rewl::SweepItem *d_items = nullptr;
     unsigned int *d_queue = nullptr;
+    std::vector<rewl::WalkerItem> walkers;   // lanes 1: single walkers of any instance
+    rewl::WalkerItem *d_walkers = nullptr;
 };
+// Batches of at least this many walkers in all run a thread per walker with its
+// state in global memory (enough walkers to fill the SMs without lane groups).
+constexpr long long kWalkerModeMin = 16384;
 
 }  // namespace
 
@@ -59,9 +64,14 @@ namespace {
 
 rewl_status enqueue_batch_round(rewl_batch_s *b, cudaStream_t s) {
     BATCH_CUDA(cudaMemsetAsync(b->d_queues, 0, sizeof(unsigned int) * b->classes.size(), s));
-    for (auto &c : b->classes)
-        BATCH_CUDA(rewl::launch_batch_sweep(c.bits, c.lanes, b->d_inst, c.d_items, (int)c.items.size(), c.d_queue,
-                                            c.grid, c.threads, c.smem, s, false));
+    for (auto &c : b->classes) {
+        if (c.lanes == 1)
+            BATCH_CUDA(rewl::launch_batch_walkers(c.bits, b->d_inst, c.d_walkers, (int)c.walkers.size(), c.grid,
+                                                  c.threads, s, false));
+        else
+            BATCH_CUDA(rewl::launch_batch_sweep(c.bits, c.lanes, b->d_inst, c.d_items, (int)c.items.size(), c.d_queue,
+                                                c.grid, c.threads, c.smem, s, false));
+    }
     BATCH_CUDA(rewl::launch_batch_check(b->d_inst, b->d_wins, b->n_wins, s));
     BATCH_CUDA(rewl::launch_batch_exchange(b->d_inst, (int)b->inst.size(), s));
     return REWL_OK;
@@ -129,26 +139,37 @@ void destroy_batch(rewl_batch_s *b) {
 extern "C" {
 
 rewl_status rewl_batch_create(const rewl_params *jobs, int n, int spin_bits, rewl_batch_t *out) {
+    return rewl_batch_create_ext(jobs, n, spin_bits, 0, out);
+}
+
+rewl_status rewl_batch_create_ext(const rewl_params *jobs, int n, int spin_bits, int lanes, rewl_batch_t *out) {
     if (!jobs || !out || n < 1) return fail(REWL_ERR_ARG, "NULL argument or n < 1");
+    if (lanes != 0 && lanes != 1 && lanes != 32) return fail(REWL_ERR_ARG, "lanes %d not 0, 1 or 32", lanes);
     *out = nullptr;
     rewl_batch_s *b = new rewl_batch_s();
     auto cleanup = [&](rewl_status s) {
         destroy_batch(b);
         return s;
     };
-    // ---- instances: parameters, sizes, plans (32 lanes per walker) -----------
+    // ---- instances: parameters, sizes, plans -----------------------------------
     size_t off = 0;
     std::vector<size_t> inst_off((size_t)n);
+    long long walkers = 0;
     for (int i = 0; i < n; ++i) {
         rewl_s *h = new rewl_s();
         h->owns = false;
         b->inst.push_back(h);
         rewl_status st = rewl::host::prepare_instance(h, jobs[i], spin_bits, 32);
         if (st) return cleanup(fail(st, "job %d: %s", i, rewl_last_error()));
-        if ((size_t)h->plan.P < 1 || rewl::fast_smem_per_walker(h->M, 32) > (size_t)h->smem_optin)
-            return cleanup(fail(REWL_ERR_ARG, "job %d: a walker does not fit in shared memory", i));
+        walkers += h->M.G;
         inst_off[(size_t)i] = off;
         off += align256(h->dbytes);
+    }
+    if (lanes == 0) lanes = walkers >= kWalkerModeMin ? 1 : 32;
+    for (int i = 0; i < n && lanes == 32; ++i) {
+        rewl_s *h = b->inst[(size_t)i];
+        if ((size_t)h->plan.P < 1 || rewl::fast_smem_per_walker(h->M, 32) > (size_t)h->smem_optin)
+            return cleanup(fail(REWL_ERR_ARG, "job %d: a walker does not fit in shared memory", i));
     }
     b->sms = b->inst[0]->sms;
     // ---- tables -------------------------------------------------------------
@@ -166,11 +187,15 @@ rewl_status rewl_batch_create(const rewl_params *jobs, int n, int spin_bits, rew
         if (cls < 0) {
             SweepClass c;
             c.bits = h->M.bits;
-            c.lanes = 32;
+            c.lanes = lanes;
             b->classes.push_back(c);
             cls = (int)b->classes.size() - 1;
         }
         SweepClass &c = b->classes[(size_t)cls];
+        if (lanes == 1) {
+            for (int g = 0; g < h->M.G; ++g) c.walkers.push_back({i, g});
+            continue;
+        }
         int P = (int)(std::max(kCtaBudget, (size_t)lay.stride) / (size_t)lay.stride);
         P = std::min(P, 256 / c.lanes);
         for (int g0 = 0; g0 < h->M.G; g0 += P) c.items.push_back({i, g0, std::min(P, h->M.G - g0), 0});
@@ -186,7 +211,8 @@ rewl_status rewl_batch_create(const rewl_params *jobs, int n, int spin_bits, rew
     std::vector<size_t> off_items;
     for (auto &c : b->classes) {
         off_items.push_back(off);
-        off += align256(c.items.size() * sizeof(rewl::SweepItem));
+        off += align256(c.lanes == 1 ? c.walkers.size() * sizeof(rewl::WalkerItem)
+                                     : c.items.size() * sizeof(rewl::SweepItem));
     }
     const size_t off_q = off;
     off += align256(b->classes.size() * sizeof(unsigned int));
@@ -213,7 +239,7 @@ rewl_status rewl_batch_create(const rewl_params *jobs, int n, int spin_bits, rew
         h->h_ctl = b->h_ctls + i;
         tab[(size_t)i].M = h->M;
         tab[(size_t)i].S = h->S;
-        tab[(size_t)i].lay = rewl::fast_layout(h->M, 32);
+        tab[(size_t)i].lay = rewl::fast_layout(h->M, lanes, lanes == 1);
         e = rewl::host::init_instance_async(h, b->stream);
     }
     if (e == cudaSuccess)
@@ -222,8 +248,16 @@ rewl_status rewl_batch_create(const rewl_params *jobs, int n, int spin_bits, rew
         e = cudaMemcpyAsync(b->d_wins, wins.data(), wins.size() * sizeof(rewl::WinItem), cudaMemcpyHostToDevice, b->stream);
     for (size_t c = 0; c < b->classes.size() && e == cudaSuccess; ++c) {
         SweepClass &k = b->classes[c];
-        k.d_items = (rewl::SweepItem *)(base + off_items[c]);
         k.d_queue = b->d_queues + c;
+        if (k.lanes == 1) {
+            k.d_walkers = (rewl::WalkerItem *)(base + off_items[c]);
+            e = cudaMemcpyAsync(k.d_walkers, k.walkers.data(), k.walkers.size() * sizeof(rewl::WalkerItem),
+                                cudaMemcpyHostToDevice, b->stream);
+            k.threads = 256;
+            k.grid = (int)((k.walkers.size() + 255) / 256);
+            continue;
+        }
+        k.d_items = (rewl::SweepItem *)(base + off_items[c]);
         e = cudaMemcpyAsync(k.d_items, k.items.data(), k.items.size() * sizeof(rewl::SweepItem), cudaMemcpyHostToDevice,
                             b->stream);
         if (e != cudaSuccess) break;

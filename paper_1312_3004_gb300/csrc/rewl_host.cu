@@ -268,7 +268,7 @@ rewl_status prepare_instance(rewl_s *h, const rewl_params &p, int spin_bits, int
                     rewl::fast_smem_per_walker(M, h->plan.lanes, h->plan.lat_global != 0), h->smem_optin);
     const size_t G = (size_t)M.G, B = (size_t)M.B, hh = (size_t)M.h;
     const size_t sizes[] = {G * M.wpc * 4, G * 4, G * 4, G * 8, G * B * 8, G * B * 4, hh * B, hh * 4, hh * 8, hh * 4, hh,
-                            G, G * 4, sizeof(Ctl)};
+                            G, G * 4, G * (B + 2 * rewl::kShadowPad) * 8, sizeof(Ctl)};
     size_t off = 0;
     h->parts.clear();
     for (size_t sz : sizes) {
@@ -296,7 +296,8 @@ void carve_instance(rewl_s *h, void *base) {
     S.done = (uint8_t *)at(10);
     S.rt_end = (uint8_t *)at(11);
     S.rt_trips = (uint32_t *)at(12);
-    S.ctl = (Ctl *)at(13);
+    S.shadow = (long long *)at(13);
+    S.ctl = (Ctl *)at(14);
 }
 
 cudaError_t init_instance_async(rewl_s *h, cudaStream_t s) {

@@ -59,6 +59,8 @@ struct State {
     uint8_t *done;        // [h] window finished
     uint8_t *rt_end;      // [G] by replica id: last end of the energy range its window touched (0, 1 low, 2 high)
     uint32_t *rt_trips;   // [G] by replica id: completed round trips (lowest window -> highest -> lowest)
+    long long *shadow;    // [G][B + 2 kShadowPad] ln g shadows of the one-lane sweep that keeps
+                          // every walker's state in global memory
     Ctl *ctl;             // control block
 };
 
@@ -81,6 +83,10 @@ struct InstDev {
 // A piece of sweep work: P walkers g0 .. g0 + P - 1 of one instance.
 struct SweepItem {
     int inst, g0, P, pad;
+};
+// One walker of one instance (the batched one-lane sweep: a thread per walker).
+struct WalkerItem {
+    int inst, g;
 };
 // A window of one instance for the batched check.
 struct WinItem {
@@ -117,6 +123,13 @@ cudaError_t launch_sweep_fast(const Model &M, const State &S, const SweepPlan &p
 Layout fast_layout(const Model &M, int lanes, bool lat_global = false);
 // A lattice above this many bytes stays in global memory in the fast sweep.
 constexpr int kSharedLatticeMax = 16384;
+// Sentinel bins beyond each end of a window in the ln g shadow.
+constexpr int kShadowPad = 24;
+// The batched one-lane sweep: every walker's state in global memory, a thread
+// per walker, walkers of any instances of one spin packing in a CTA.
+cudaError_t launch_batch_walkers(int bits, const InstDev *inst, const WalkerItem *items, int n_items, int grid,
+                                 int threads, cudaStream_t s, bool prepare);
+int batch_walkers_ctas_per_sm(int bits, int threads);
 cudaError_t launch_batch_check(const InstDev *inst, const WinItem *wins, int n_wins, cudaStream_t s);
 cudaError_t launch_batch_exchange(const InstDev *inst, int n_inst, cudaStream_t s);
 // Persistent batched sweep for one (spin bits, lanes) class: CTAs of `threads`

@@ -485,7 +485,7 @@ SweepPlan plan_sweep(const Model &M, int num_sms, size_t smem_optin, int kind, i
         p.lanes = lanes;
         p.lat_global = lat_mode == 1 ? 1 : lat_mode == 2 ? 0 : (M.wpc * 4 > kSharedLatticeMax ? 1 : 0);
         const size_t per = fast_smem_per_walker(M, lanes, p.lat_global != 0);
-        int cap = (int)(smem_optin / per);
+        int cap = per ? (int)(smem_optin / per) : 256;  // per = 0: nothing in shared memory
         if (cap > 256 / lanes) cap = 256 / lanes;
         int P = (M.G + num_sms - 1) / num_sms;
         if (P < 1) P = 1;

@@ -95,7 +95,7 @@ constexpr long long kNoReject = 1LL << 62;
 // padding also covers the loads of speculative paths (up to six moves of up
 // to four bins each, see the step tree below).
 constexpr long long kOutside = 0x7fffffffffffffffLL;
-constexpr int kPad = 24;
+constexpr int kPad = kShadowPad;
 constexpr long long kMant = (1LL << 52) - 1, kHidden = 1LL << 52;
 
 // floor / ceil of x * 2^k as a 64-bit integer, saturating at 2^61 (x >= 0).
@@ -295,7 +295,8 @@ __device__ void walker_sweep(const Model &M, uint32_t *__restrict__ lat, long lo
     // to lgf[Eo]), pcur the shared address of lgf[Eo].  A shadow >= 2^52 is the
     // value exactly; below that the exact binary64 bits are kept in lgb.
     int Eo = E_io - lo;
-    const uint32_t pbase = (uint32_t)__cvta_generic_to_shared(lgf);
+    // (lane groups: the shadow is in shared memory; one lane: shared or global)
+    const uint32_t pbase = S > 1 ? (uint32_t)__cvta_generic_to_shared(lgf) : 0u;
     long long AF = lgf[Eo];
     unsigned int nacc = 0;
     // node of this lane in the step tree (lane S - 1 has none)
@@ -385,8 +386,8 @@ __device__ void walker_sweep(const Model &M, uint32_t *__restrict__ lat, long lo
                     // The step is computed speculatively; a step that needs more (a
                     // draw inside the bracket, a value with dropped bits, a binade
                     // crossing) leaves the loop before it changes anything.
-                    const uint32_t pn = pcur + (uint32_t)(dE * 8);
-                    const long long BF = lds64(pn);  // beyond the window: kOutside
+                    const int En = Eo + dE;
+                    const long long BF = lgf[En];  // beyond the window: kOutside
                     const long long D = BF - AF;
                     const bool acc = D < q1.x;
                     const bool unsure = (unsigned long long)D - (unsigned long long)q1.x < (unsigned long long)q1.y;
@@ -395,9 +396,9 @@ __device__ void walker_sweep(const Model &M, uint32_t *__restrict__ lat, long lo
                     const uint32_t hc = (uint32_t)((unsigned long long)cur >> 32);
                     const uint32_t h2 = (uint32_t)((unsigned long long)AF2 >> 32);
                     if (!(unsure || (cur & 1) || (h2 ^ hc) > hc)) {
-                        pcur = acc ? pn : pcur;
+                        Eo = acc ? En : Eo;
                         AF = AF2;
-                        sts64(pcur, AF);
+                        lgf[Eo] = AF;
                         accm |= acc ? 1u : 0u;
                         kk = 1;
                     }
@@ -496,7 +497,7 @@ __device__ void walker_sweep(const Model &M, uint32_t *__restrict__ lat, long lo
                         if (c < m || kk >= n) break;
                     }
                 }
-                Eo = (int)((pcur - pbase) >> 3);
+                if constexpr (S > 1) Eo = (int)((pcur - pbase) >> 3);
                 if (kk >= n) break;
             }
             if (S > 1 && int_add && ((flagm >> kk) & 1u)) {
@@ -651,9 +652,11 @@ __device__ void sweep_block(const Model &M, const State &Sg, int g0, int P, cons
         int E = Sg.cfg_E[c];
         unsigned long long t = Sg.t[g];
         uint32_t *lat = LG ? Sg.spins + (size_t)c * M.wpc : reinterpret_cast<uint32_t *>(base + lay.off_lat);
-        walker_sweep<BITS, S>(M, lat, reinterpret_cast<long long *>(Sg.lng + (size_t)g * M.B),
-                              reinterpret_cast<long long *>(base + lay.off_lgf) + kPad, Sg.H + (size_t)g * M.B, st,
-                              g, Sg.e_lo[w], Sg.lnf[w], E, t, tally);
+        // one lane with global lattices: the shadow is in global memory too
+        long long *lgf = (S == 1 && LG) ? Sg.shadow + (size_t)g * (M.B + 2 * kPad) + kPad
+                                        : reinterpret_cast<long long *>(base + lay.off_lgf) + kPad;
+        walker_sweep<BITS, S>(M, lat, reinterpret_cast<long long *>(Sg.lng + (size_t)g * M.B), lgf,
+                              Sg.H + (size_t)g * M.B, st, g, Sg.e_lo[w], Sg.lnf[w], E, t, tally);
         if ((threadIdx.x & (S - 1)) == 0) {
             Sg.cfg_E[c] = E;
             Sg.t[g] = t;
@@ -703,10 +706,47 @@ __global__ void __launch_bounds__(256) batch_sweep_kernel(const InstDev *inst, c
     }
 }
 
+// Batched one-lane sweep with every walker's state in global memory: thread i
+// runs walker items[i] (any instance of this spin packing) for K steps.
+template <int BITS>
+__global__ void __launch_bounds__(256) batch_walker_kernel(const InstDev *inst, const WalkerItem *items, int n_items) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_items) return;
+    const WalkerItem it = items[i];
+    const Model &M = inst[it.inst].M;
+    const State &Sg = inst[it.inst].S;
+    if (*(volatile unsigned int *)&Sg.ctl->all_done) return;
+    const int g = it.g;
+    if (Sg.done[g / M.m]) return;
+    const Model Mr = M;
+    const State Sr = Sg;
+    Stage st{};
+    Tally tally{0ull, 0ull, 0u, 0u};
+    const int w = g / Mr.m;
+    const uint32_t c = Sr.slot_cfg[g];
+    int E = Sr.cfg_E[c];
+    unsigned long long t = Sr.t[g];
+    walker_sweep<BITS, 1>(Mr, Sr.spins + (size_t)c * Mr.wpc, reinterpret_cast<long long *>(Sr.lng + (size_t)g * Mr.B),
+                          Sr.shadow + (size_t)g * (Mr.B + 2 * kPad) + kPad, Sr.H + (size_t)g * Mr.B, st, g, Sr.e_lo[w],
+                          Sr.lnf[w], E, t, tally);
+    Sr.cfg_E[c] = E;
+    Sr.t[g] = t;
+    atomicAdd(&Sr.ctl->flips, (unsigned long long)Mr.K);
+    atomicAdd(&Sr.ctl->accepted, (unsigned long long)tally.acc);
+    if (tally.slow) atomicAdd(&Sr.ctl->slow, tally.slow);
+    if (tally.ties) atomicAdd(&Sr.ctl->ties, tally.ties);
+    if (tally.seq) atomicAdd(&Sr.ctl->seq, (unsigned long long)tally.seq);
+}
+
 Layout make_layout(const Model &M, int S, bool lat_global) {
     auto al = [](int x) { return (x + 15) & ~15; };
     Layout l{};
     int off = 0;
+    if (S == 1 && lat_global) {  // every part of the walker's state in global memory
+        l.off_lgf = l.off_lat = l.off_q = l.off_e = l.off_bm = -1;
+        l.stride = 0;
+        return l;
+    }
     l.off_lgf = off;
     off += al((M.B + 2 * kPad) * 8);
     l.off_lat = -1;
@@ -821,6 +861,22 @@ int batch_sweep_ctas_per_sm(int bits, int lanes, int threads, size_t smem) {
     case 16: return occupancy_t<4, 16>(threads, smem);
     default: return occupancy_t<4, 32>(threads, smem);
     }
+}
+
+cudaError_t launch_batch_walkers(int bits, const InstDev *inst, const WalkerItem *items, int n_items, int grid,
+                                 int threads, cudaStream_t s, bool prepare) {
+    if (prepare) return cudaSuccess;
+    if (n_items <= 0) return cudaSuccess;
+    if (bits == 8) fast::batch_walker_kernel<8><<<grid, threads, 0, s>>>(inst, items, n_items);
+    else fast::batch_walker_kernel<4><<<grid, threads, 0, s>>>(inst, items, n_items);
+    return cudaGetLastError();
+}
+
+int batch_walkers_ctas_per_sm(int bits, int threads) {
+    int n = 0;
+    cudaError_t e = bits == 8 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fast::batch_walker_kernel<8>, threads, 0)
+                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fast::batch_walker_kernel<4>, threads, 0);
+    return e == cudaSuccess ? n : 0;
 }
 
 cudaError_t launch_sweep_fast(const Model &M, const State &S, const SweepPlan &p, cudaStream_t s, bool prepare) {

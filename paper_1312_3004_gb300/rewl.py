@@ -154,10 +154,11 @@ class Batch:
 
     jobs: sequence of dicts with the REWL parameters (q, L, h, overlap, m,
     lnf_final, flatness, exchange_interval, seed).  Each instance computes the
-    same states as it would alone.
+    same states as it would alone.  lanes: 32 (lane groups, shared memory),
+    1 (a thread per walker, state in global memory) or 0 (chosen by size).
     """
 
-    def __init__(self, jobs, spin_bits=0, stream=None):
+    def __init__(self, jobs, spin_bits=0, stream=None, lanes=0):
         self._L = _lib.load()
         self._h = C.c_void_p()
         self.jobs = [dict(j) for j in jobs]
@@ -165,7 +166,7 @@ class Batch:
         for i, j in enumerate(self.jobs):
             arr[i] = _lib.Params(j["q"], j["L"], j["h"], j["overlap"], j["m"], j["lnf_final"],
                                  j["flatness"], j["exchange_interval"], j["seed"])
-        check(self._L.rewl_batch_create(arr, len(self.jobs), spin_bits, C.byref(self._h)))
+        check(self._L.rewl_batch_create_ext(arr, len(self.jobs), spin_bits, lanes, C.byref(self._h)))
         if stream is not None:
             self.set_stream(stream)
         self._views = {}

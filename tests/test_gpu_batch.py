@@ -11,7 +11,8 @@ from paper_1312_3004_gb300 import workloads as WL
 
 pytestmark = pytest.mark.gpu
 
-FIELDS = ("spins", "energy", "replica", "steps", "lng", "hist", "mask", "lnf", "iter", "done", "round")
+FIELDS = ("spins", "energy", "replica", "steps", "lng", "hist", "mask", "lnf", "iter", "done", "round", "trips",
+          "trip_end")
 
 
 def jobs_mixed():
@@ -32,9 +33,12 @@ def alone(j, rounds):
     return r
 
 
-def test_batched_instances_equal_their_runs_alone():
+@pytest.mark.parametrize("lanes", [32, 1])
+def test_batched_instances_equal_their_runs_alone(lanes):
+    """Both mappings of walkers to threads: lane groups with shared-memory
+    staging, and a thread per walker with every state in global memory."""
     jobs = jobs_mixed()
-    b = Batch(jobs)
+    b = Batch(jobs, lanes=lanes)
     assert b.info()["instances"] == len(jobs)
     for rounds in (1, 4, 9):
         b.run(rounds)
@@ -45,9 +49,10 @@ def test_batched_instances_equal_their_runs_alone():
             assert np.array_equal(v.get(f), a.get(f)), (i, f)
 
 
-def test_batched_instances_equal_the_oracle():
+@pytest.mark.parametrize("lanes", [32, 1])
+def test_batched_instances_equal_the_oracle(lanes):
     jobs = jobs_mixed()[:5]
-    b = Batch(jobs)
+    b = Batch(jobs, lanes=lanes)
     b.run(6)
     for i, j in enumerate(jobs):
         orc = O.OracleREWL(*WL.rewl_args(j, j["seed"]))
