@@ -146,11 +146,15 @@ rewl_status rewl_run_phase(rewl_t h, int phase);
  *   REWL_OPT_SWEEP_KERNEL  0 = fast sweep (integer acceptance path with a
  *                          binary64 fallback), 1 = binary64 reference sweep
  *   REWL_OPT_LANES         lanes per walker of the fast sweep: 0 = chosen from
- *                          the walker count, or 1, 2, 4, 8, 16, 32
+ *                          the walker count (32 up to 80 per SM, else 1), or
+ *                          1, 2, 4, 8, 16, 32
  *   REWL_OPT_WALKERS_PER_CTA  (read-only) walkers per CTA of the current plan
  *   REWL_OPT_LATTICE       where the fast sweep keeps the lattices: set 0 =
- *                          chosen from their size (shared memory up to 16 KB
- *                          each), 1 = global memory (L2), 2 = shared memory;
+ *                          chosen (global memory above 16 KB each, and with
+ *                          one lane per walker; else shared memory), 1 =
+ *                          global memory (L2), 2 = shared memory; with one
+ *                          lane per walker, global means the walker's whole
+ *                          state (its ln g shadow too) stays in global memory;
  *                          get: 1 if the current plan keeps them in global
  *                          memory, else 0
  * rewl_set_option synchronises the stream and re-plans the sweep.

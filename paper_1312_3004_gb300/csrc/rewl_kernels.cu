@@ -481,9 +481,15 @@ SweepPlan plan_sweep(const Model &M, int num_sms, size_t smem_optin, int kind, i
     SweepPlan p{};
     p.kind = kind;
     if (kind == SWEEP_FAST) {
-        if (lanes <= 0) lanes = M.G <= 16 * num_sms ? 32 : (M.G <= 64 * num_sms ? 8 : 1);
+        // lane groups while walkers are few (each walker's chain is what bounds
+        // the rate); a thread per walker, state in global memory, once there are
+        // enough of them to fill the SMs by themselves (measured crossover on
+        // GB300: between 4096 and 16384 walkers)
+        if (lanes <= 0) lanes = M.G <= 80 * num_sms ? 32 : 1;
         p.lanes = lanes;
-        p.lat_global = lat_mode == 1 ? 1 : lat_mode == 2 ? 0 : (M.wpc * 4 > kSharedLatticeMax ? 1 : 0);
+        p.lat_global = lat_mode == 1   ? 1
+                       : lat_mode == 2 ? 0
+                                       : ((M.wpc * 4 > kSharedLatticeMax || lanes == 1) ? 1 : 0);
         const size_t per = fast_smem_per_walker(M, lanes, p.lat_global != 0);
         int cap = per ? (int)(smem_optin / per) : 256;  // per = 0: nothing in shared memory
         if (cap > 256 / lanes) cap = 256 / lanes;

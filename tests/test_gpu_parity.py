@@ -267,3 +267,19 @@ def test_spins_roundtrip_and_energy_recount():
     E = gpu.get("energy")
     for g in range(s2.shape[0]):
         assert E[g] == O.energy(11, s2[g])
+
+
+def test_many_walkers_run_a_thread_each_with_global_state():
+    """Above 80 walkers per SM the plan maps a thread to each walker with its
+    whole state in global memory; the states still match the oracle."""
+    from paper_1312_3004_gb300 import _lib
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    m = 256
+    h = max(2, (80 * sms) // m + 1)
+    gpu, orc = make_pair(10, 12, h, 0.75, m, 1e-6, 0.8, 150, 21, spin_bits=8)
+    assert gpu.G > 80 * sms
+    assert gpu.get_option(_lib.OPT_LANES) == 1 and gpu.get_option(_lib.OPT_LATTICE) == 1
+    for n in (1, 2):
+        run_both(gpu, orc, n)
+        assert_parity(gpu, orc)
