@@ -567,8 +567,7 @@ __device__ void walker_sweep(const Model &M, uint32_t *__restrict__ lat, long lo
             lgf[Eo] = AF;
             pcur = pbase + (uint32_t)Eo * 8u;
             if (acc) {
-                if (S == 1) lat[kword] ^= kxr;
-                else if (j == 0) atomicXor(&lat[kword], kxr);
+                if (S == 1 || j == 0) atomicXor(&lat[kword], kxr);
                 accm |= 1u << kk;
             }
             done |= accm & (1u << kk);
@@ -577,10 +576,8 @@ __device__ void walker_sweep(const Model &M, uint32_t *__restrict__ lat, long lo
         }
 
         // ---- after the batch: lattice and histogram ----------------------------
-        if (((accm & ~done) >> j) & 1u) {
-            if (S == 1) lat[word] ^= xr;
-            else atomicXor(&lat[word], xr);
-        }
+        // (atomics whose result is not used: the walker does not wait for them)
+        if (((accm & ~done) >> j) & 1u) atomicXor(&lat[word], xr);
         // the bin after step j: the batch's start plus the accepted moves up to j
         int x = (j < n && ((accm >> j) & 1u)) ? dE : 0;
 #pragma unroll
@@ -590,7 +587,7 @@ __device__ void walker_sweep(const Model &M, uint32_t *__restrict__ lat, long lo
         }
         const int bin = Eb + x;
         if (S == 1) {
-            hg[bin] += 1u;
+            atomicAdd(&hg[bin], 1u);
         } else {  // one add per run of equal bins, by the run's last step
             const int nxt = __shfl_down_sync(gm, bin, 1, S);
             const bool last = j < n && (j == n - 1 || nxt != bin);
