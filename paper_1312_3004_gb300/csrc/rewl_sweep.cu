@@ -256,10 +256,127 @@ __device__ __forceinline__ T from_lane(unsigned gm, T x, int k) {
     return __shfl_sync(gm, x, k, S);
 }
 
+// One lane per walker: the steps one after another, each proposal drawn (and
+// its spins read) while the previous step waits for its ln g shadow; a
+// proposal whose site or neighbours the previous step flipped is re-read.
+// The frame, the shadow, the bracket and the exact fallbacks are those of
+// walker_sweep below.
+template <int BITS>
+__device__ void walker_sweep_1(const Model &M, uint32_t *__restrict__ lat, long long *__restrict__ lgb, long long *lgf,
+                               uint32_t *__restrict__ hg, int g, int lo, double lnf, int &E_io,
+                               unsigned long long &t_io, Tally &tally) {
+    const int N = M.N, L = M.L;
+    constexpr int per = 32 / BITS;
+    const uint32_t qm1 = (uint32_t)(M.q - 1);
+    const long long LNF = __double_as_longlong(lnf);
+    long long vmax = 0;
+    for (int b = 0; b < M.B; ++b) vmax = max(vmax, lgb[b]);
+    const double reach = __dadd_rn(__longlong_as_double(vmax), __dmul_rn((double)M.K, lnf));
+    int ew = (int)(__double_as_longlong(reach) >> 52) - 7;
+    if (ew < 1) ew = 1;
+    const int k = 1076 - ew;
+    for (int b = 0; b < M.B; ++b) lgf[b] = shadow_of(lgb[b], ew);
+    for (int p = 0; p < kPad; ++p) {
+        lgf[-1 - p] = kOutside;
+        lgf[M.B + p] = kOutside;
+    }
+    bool addF;
+    const long long incU = exact_units(LNF, ew, addF);
+    const long long incF = incU << 1;
+    const bool int_add = addF && (incU & 255) == 0;
+
+    struct Prop {
+        int site, v, cur, sr, sl, sd, su;
+        Site4 nb;
+        longlong2 th;
+        unsigned long long U;
+    };
+    auto draw = [&](unsigned long long tt, Prop &p) {
+        const uint4 r = philox((uint32_t)tt, (uint32_t)(tt >> 32), (uint32_t)g, DOM_WL, M.key0, M.key1);
+        p.site = (int)__umulhi(r.x, (uint32_t)N);
+        p.v = (int)__umulhi(r.y, qm1);
+        p.nb = nbrs(p.site, L, N, M.divL);
+        p.cur = spin_get<BITS>(lat, p.site);
+        p.sr = spin_get<BITS>(lat, p.nb.r);
+        p.sl = spin_get<BITS>(lat, p.nb.l);
+        p.sd = spin_get<BITS>(lat, p.nb.d);
+        p.su = spin_get<BITS>(lat, p.nb.u);
+        p.U = u53(r.z, r.w);
+        accept_bracket(p.U, k, p.th.x, p.th.y);
+    };
+    int Eo = E_io - lo;
+    long long AF = lgf[Eo];
+    unsigned int nacc = 0;
+    int flipped = -1;  // site the previous step flipped
+    Prop cp;
+    draw(t_io, cp);
+    for (long long i = 0; i < M.K; ++i) {
+        if (flipped >= 0 && (flipped == cp.site || flipped == cp.nb.r || flipped == cp.nb.l || flipped == cp.nb.d ||
+                             flipped == cp.nb.u)) {
+            cp.cur = spin_get<BITS>(lat, cp.site);
+            cp.sr = spin_get<BITS>(lat, cp.nb.r);
+            cp.sl = spin_get<BITS>(lat, cp.nb.l);
+            cp.sd = spin_get<BITS>(lat, cp.nb.d);
+            cp.su = spin_get<BITS>(lat, cp.nb.u);
+        }
+        const int nw = cp.v + (cp.v >= cp.cur);
+        const int dE = (int)(cp.sr == cp.cur) + (int)(cp.sl == cp.cur) + (int)(cp.sd == cp.cur) + (int)(cp.su == cp.cur) -
+                       (int)(cp.sr == nw) - (int)(cp.sl == nw) - (int)(cp.sd == nw) - (int)(cp.su == nw);
+        const int En = Eo + dE;
+        const long long BF = lgf[En];  // beyond the window: kOutside
+        Prop np;
+        if (i + 1 < M.K) draw(t_io + (unsigned long long)i + 1ull, np);
+        const long long D = BF - AF;
+        bool acc = D < cp.th.x;
+        if (!acc && D < cp.th.y) {  // inside the bracket (never beyond the window)
+            tally.slow += 1;
+            const long long Ab = (AF & 1) ? lgb[Eo] : from_units(AF >> 1, ew);
+            const long long Bb = (BF & 1) ? lgb[En] : from_units(BF >> 1, ew);
+            acc = dE == 0 ? true : exact_accept(Ab, Bb, cp.U, &tally.ties);
+        }
+        const long long cur = acc ? BF : AF;  // with dE = 0 both are the current shadow
+        const int Eb2 = acc ? En : Eo;
+        long long AF2 = cur + incF;
+        if (!int_add || (cur & 1)) {  // ln g(E) += ln f in binary64
+            tally.seq += 1;
+            const long long Ab = (cur & 1) ? lgb[Eb2] : from_units(cur >> 1, ew);
+            const long long A2 = exact_add(Ab, lnf);
+            lgb[Eb2] = A2;
+            AF2 = shadow_of(A2, ew);
+        } else {
+            const uint32_t hc = (uint32_t)((unsigned long long)cur >> 32);
+            const uint32_t h2 = (uint32_t)((unsigned long long)AF2 >> 32);
+            if ((h2 ^ hc) > hc) AF2 = round_shadow(AF2);  // into the next binade
+        }
+        Eo = Eb2;
+        AF = AF2;
+        lgf[Eo] = AF;
+        // (atomics whose result is not used: the walker does not wait for them)
+        if (acc) {
+            atomicXor(&lat[cp.site / per], (uint32_t)(cp.cur ^ nw) << ((cp.site & (per - 1)) * BITS));
+            ++nacc;
+        }
+        flipped = acc ? cp.site : -1;
+        atomicAdd(&hg[Eo], 1u);
+        cp = np;
+    }
+    t_io += (unsigned long long)M.K;
+    for (int b = 0; b < M.B; ++b) {
+        const long long F = lgf[b];
+        if (!(F & 1)) lgb[b] = from_units(F >> 1, ew);
+    }
+    tally.acc += nacc;
+    E_io = Eo + lo;
+}
+
 template <int BITS, int S>
 __device__ void walker_sweep(const Model &M, uint32_t *__restrict__ lat, long long *__restrict__ lgb,
                              long long *lgf, uint32_t *__restrict__ hg, const Stage &st, int g, int lo,
                              double lnf, int &E_io, unsigned long long &t_io, Tally &tally) {
+    if constexpr (S == 1) {
+        walker_sweep_1<BITS>(M, lat, lgb, lgf, hg, g, lo, lnf, E_io, t_io, tally);
+        return;
+    }
     const int j = (int)(threadIdx.x & (unsigned)(S - 1));
     const unsigned gm = group_mask<S>();
     const int N = M.N, L = M.L;
