@@ -304,8 +304,11 @@ __device__ void walker_sweep_1(const Model &M, uint32_t *__restrict__ lat, long 
         p.U = u53(r.z, r.w);
         accept_bracket(p.U, k, p.th.x, p.th.y);
     };
+    // The current bin's shadow AF and its visits since the walker came are kept
+    // in registers, and written when the walker leaves the bin.
     int Eo = E_io - lo;
     long long AF = lgf[Eo];
+    uint32_t visits = 0;
     unsigned int nacc = 0;
     int flipped = -1;  // site the previous step flipped
     Prop cp;
@@ -323,7 +326,7 @@ __device__ void walker_sweep_1(const Model &M, uint32_t *__restrict__ lat, long 
         const int dE = (int)(cp.sr == cp.cur) + (int)(cp.sl == cp.cur) + (int)(cp.sd == cp.cur) + (int)(cp.su == cp.cur) -
                        (int)(cp.sr == nw) - (int)(cp.sl == nw) - (int)(cp.sd == nw) - (int)(cp.su == nw);
         const int En = Eo + dE;
-        const long long BF = lgf[En];  // beyond the window: kOutside
+        const long long BF = dE == 0 ? AF : lgf[En];  // beyond the window: kOutside
         Prop np;
         if (i + 1 < M.K) draw(t_io + (unsigned long long)i + 1ull, np);
         const long long D = BF - AF;
@@ -348,18 +351,24 @@ __device__ void walker_sweep_1(const Model &M, uint32_t *__restrict__ lat, long 
             const uint32_t h2 = (uint32_t)((unsigned long long)AF2 >> 32);
             if ((h2 ^ hc) > hc) AF2 = round_shadow(AF2);  // into the next binade
         }
+        // (atomics whose result is not used: the walker does not wait for them)
+        if (Eb2 != Eo) {  // leaving the bin: its value and visits go to memory
+            lgf[Eo] = AF;
+            atomicAdd(&hg[Eo], visits);
+            visits = 0;
+        }
+        ++visits;
         Eo = Eb2;
         AF = AF2;
-        lgf[Eo] = AF;
-        // (atomics whose result is not used: the walker does not wait for them)
         if (acc) {
             atomicXor(&lat[cp.site / per], (uint32_t)(cp.cur ^ nw) << ((cp.site & (per - 1)) * BITS));
             ++nacc;
         }
         flipped = acc ? cp.site : -1;
-        atomicAdd(&hg[Eo], 1u);
         cp = np;
     }
+    lgf[Eo] = AF;
+    atomicAdd(&hg[Eo], visits);
     t_io += (unsigned long long)M.K;
     for (int b = 0; b < M.B; ++b) {
         const long long F = lgf[b];
