@@ -248,8 +248,9 @@ rewl_status rewl_batch_create(const rewl_params *jobs, int n, int spin_bits, rew
  * group of 32 lanes per walker with its state staged in shared memory (walker
  * groups of one instance per CTA); lanes = 1, a thread per walker with all its
  * state in global memory (walkers of any instances in a CTA); lanes = 0,
- * chosen from the total walker count (1 from 16384 walkers on).  Results are
- * the same either way.  Errors: REWL_ERR_ARG for another lanes value. */
+ * chosen from the total walker count (1 from 16384 walkers on).  With one lane
+ * and spin_bits = 0 the spins are packed 8 bits each.  Results are the same
+ * either way.  Errors: REWL_ERR_ARG for another lanes value. */
 rewl_status rewl_batch_create_ext(const rewl_params *jobs, int n, int spin_bits, int lanes, rewl_batch_t *out);
 
 /* Run rounds of every unfinished instance until all have converged or

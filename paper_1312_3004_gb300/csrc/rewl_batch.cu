@@ -152,20 +152,22 @@ rewl_status rewl_batch_create_ext(const rewl_params *jobs, int n, int spin_bits,
         return s;
     };
     // ---- instances: parameters, sizes, plans -----------------------------------
+    long long walkers = 0;
+    for (int i = 0; i < n; ++i) walkers += (long long)std::max(jobs[i].h, 0) * std::max(jobs[i].m, 0);
+    if (lanes == 0) lanes = walkers >= kWalkerModeMin ? 1 : 32;
+    // a thread per walker reads whole bytes faster than 4-bit fields
+    const int bits = (spin_bits == 0 && lanes == 1) ? 8 : spin_bits;
     size_t off = 0;
     std::vector<size_t> inst_off((size_t)n);
-    long long walkers = 0;
     for (int i = 0; i < n; ++i) {
         rewl_s *h = new rewl_s();
         h->owns = false;
         b->inst.push_back(h);
-        rewl_status st = rewl::host::prepare_instance(h, jobs[i], spin_bits, 32);
+        rewl_status st = rewl::host::prepare_instance(h, jobs[i], bits, 32);
         if (st) return cleanup(fail(st, "job %d: %s", i, rewl_last_error()));
-        walkers += h->M.G;
         inst_off[(size_t)i] = off;
         off += align256(h->dbytes);
     }
-    if (lanes == 0) lanes = walkers >= kWalkerModeMin ? 1 : 32;
     for (int i = 0; i < n && lanes == 32; ++i) {
         rewl_s *h = b->inst[(size_t)i];
         if ((size_t)h->plan.P < 1 || rewl::fast_smem_per_walker(h->M, 32) > (size_t)h->smem_optin)
