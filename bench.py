@@ -386,6 +386,10 @@ def run_batched(args):
                       "form": "one instance per launch, instances one after another"},
             "batched_over_plain": value / plain, "gpu_launches": 3 * args.steps,
             "mapping": "thread per walker, state in global memory",
+            "roofline": {"bound": "alu", "achieved": value * ALG_OPS_PER_FLIP / 1e12,
+                         "peak": SMS * LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12, "unit": "Tops/s",
+                         "frac": value * ALG_OPS_PER_FLIP / (SMS * LANES_PER_SM * SM_MAX_MHZ * 1e6),
+                         "traffic": None, "ops_per_flip": ALG_OPS_PER_FLIP},
             "lane_groups": {"value": groups, "unit": "flips/s",
                             "form": "32 lanes per walker, state staged in shared memory"}}
     print(json.dumps(line), flush=True)

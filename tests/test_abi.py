@@ -89,6 +89,9 @@ def test_batch_arguments_are_checked_before_any_device_work():
     assert b"job 0" in lib.rewl_last_error()
     wide = (_lib.Params * 1)(params(q=17))
     assert lib.rewl_batch_create(wide, 1, 4, C.byref(out)) == 1  # q > 16 cannot pack in 4 bits
+    ok = (_lib.Params * 1)(params())
+    assert lib.rewl_batch_create_ext(ok, 1, 0, 3, C.byref(out)) == 1  # lanes must be 0, 1 or 32
+    assert b"lanes" in lib.rewl_last_error()
     assert lib.rewl_batch_run(None, 1, None) == 1
     lib.rewl_batch_destroy(None)
 
