@@ -50,7 +50,7 @@ typedef enum {
     REWL_ERR_ARG = 1,       /* an argument is out of range or a pointer is NULL   */
     REWL_ERR_NOMEM = 2,     /* a device or host allocation failed                 */
     REWL_ERR_CUDA = 3,      /* a CUDA runtime call failed                          */
-    REWL_ERR_TIMEOUT = 4,   /* a bounded device wait gave up                       */
+    REWL_ERR_TIMEOUT = 4,   /* the stall watchdog gave up (REWL_OPT_STALL_MS)      */
     REWL_ERR_OVERFLOW = 5,  /* a histogram bin reached 2^31 visits                 */
     REWL_ERR_STATE = 6,     /* call not valid in the current state (see function) */
     REWL_ERR_CANCELLED = 7  /* the job was cancelled                               */
@@ -157,10 +157,19 @@ rewl_status rewl_run_phase(rewl_t h, int phase);
  *                          state (its ln g shadow too) stays in global memory;
  *                          get: 1 if the current plan keeps them in global
  *                          memory, else 0
- * rewl_set_option synchronises the stream and re-plans the sweep.
+ *   REWL_OPT_STALL_MS      stall watchdog of rewl_run: when no window has
+ *                          finished an iteration for this many milliseconds
+ *                          of the call, rewl_run stops at a round boundary
+ *                          and returns REWL_ERR_TIMEOUT (the state stays valid
+ *                          and the run can go on); 0 (default) = off
+ * rewl_set_option synchronises the stream and re-plans the sweep (not for
+ * REWL_OPT_STALL_MS).
  * Errors: REWL_ERR_ARG (unknown option or value, or a plan that does not fit
  * in shared memory). */
-enum { REWL_OPT_SWEEP_KERNEL = 0, REWL_OPT_LANES = 1, REWL_OPT_WALKERS_PER_CTA = 2, REWL_OPT_LATTICE = 3 };
+enum {
+    REWL_OPT_SWEEP_KERNEL = 0, REWL_OPT_LANES = 1, REWL_OPT_WALKERS_PER_CTA = 2, REWL_OPT_LATTICE = 3,
+    REWL_OPT_STALL_MS = 4
+};
 rewl_status rewl_set_option(rewl_t h, int option, long long value);
 rewl_status rewl_get_option(rewl_t h, int option, long long *value);
 
@@ -352,6 +361,17 @@ rewl_status rewl_run_static(const rewl_params *params, int spin_bits, long long 
 
 /* Release the handle and its device memory.  NULL is ignored. */
 void rewl_destroy(rewl_t h);
+
+/* Device memory source for the handles, batches and servers created from now
+ * on (no counterpart in the paper: it lets a framework's caching allocator, or
+ * a fixed budget, supply the state arrays).  alloc(bytes, ctx) returns device
+ * memory of the current device aligned to 256 bytes, or NULL; free(ptr, ctx)
+ * takes back what alloc returned (NULL: the allocator keeps it).  alloc = NULL
+ * restores cudaMalloc / cudaFree.  Each object frees its memory through the
+ * allocator that gave it, so the source can change while objects live.  Not
+ * safe to call while another thread creates objects.  A NULL return (or a
+ * misaligned pointer) makes the creating call fail with REWL_ERR_NOMEM. */
+void rewl_set_allocator(void *(*alloc)(size_t bytes, void *ctx), void (*free)(void *ptr, void *ctx), void *ctx);
 
 /* Message of the last error on this thread ("" if none). */
 const char *rewl_last_error(void);

@@ -16,7 +16,7 @@ STATUS_NAMES = {0: "REWL_OK", 1: "REWL_ERR_ARG", 2: "REWL_ERR_NOMEM", 3: "REWL_E
 
 FIELD_SPINS, FIELD_ENERGY, FIELD_REPLICA, FIELD_STEPS, FIELD_LNG, FIELD_HIST = 0, 1, 2, 3, 4, 5
 PHASE_SWEEP, PHASE_CHECK, PHASE_EXCHANGE = 0, 1, 2
-OPT_SWEEP_KERNEL, OPT_LANES, OPT_WALKERS_PER_CTA, OPT_LATTICE = 0, 1, 2, 3
+OPT_SWEEP_KERNEL, OPT_LANES, OPT_WALKERS_PER_CTA, OPT_LATTICE, OPT_STALL_MS = 0, 1, 2, 3, 4
 FIELD_MASK, FIELD_LNF, FIELD_ITER, FIELD_DONE, FIELD_ELO, FIELD_ROUND = 6, 7, 8, 9, 10, 11
 FIELD_TRIPS, FIELD_TRIP_END = 12, 13
 
@@ -48,6 +48,10 @@ class Stats(C.Structure):
 
 _lib = None
 
+# rewl_set_allocator callbacks: alloc(bytes, ctx) -> device pointer or NULL; free(ptr, ctx)
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
 
 def load():
     """Load librewl.so; raises if it has not been built."""
@@ -62,6 +66,8 @@ def load():
     st = C.c_int
     L.rewl_create.argtypes = [i32, i32, i32, dbl, i32, dbl, dbl, ll, C.c_ulonglong, C.POINTER(H)]
     L.rewl_create_ext.argtypes = [C.POINTER(Params), i32, C.POINTER(H)]
+    L.rewl_set_allocator.argtypes = [ALLOC_FN, FREE_FN, vp]
+    L.rewl_set_allocator.restype = None
     L.rewl_set_stream.argtypes = [H, vp]
     L.rewl_run.argtypes = [H, ll, C.POINTER(C.c_int)]
     L.rewl_run_async.argtypes = [H, ll]

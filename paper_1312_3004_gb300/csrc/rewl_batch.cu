@@ -47,6 +47,7 @@ constexpr long long kWalkerModeMin = 16384;
 struct rewl_batch_s {
     std::vector<rewl_s *> inst;
     void *dmem = nullptr;
+    rewl::host::DevBlock dblock;
     size_t dbytes = 0;
     rewl::Ctl *h_ctls = nullptr;  // pinned mirrors of every instance's control block
     rewl::Ctl *d_ctls = nullptr;  // the control blocks, contiguous
@@ -130,7 +131,7 @@ void destroy_batch(rewl_batch_s *b) {
     for (rewl_s *h : b->inst) delete h;
     if (b->own_stream) cudaStreamDestroy(b->own_stream);
     if (b->h_ctls) cudaFreeHost(b->h_ctls);
-    if (b->dmem) cudaFree(b->dmem);
+    rewl::host::dev_free(b->dblock);
     delete b;
 }
 
@@ -219,8 +220,10 @@ rewl_status rewl_batch_create_ext(const rewl_params *jobs, int n, int spin_bits,
     const size_t off_q = off;
     off += align256(b->classes.size() * sizeof(unsigned int));
     b->dbytes = off;
-    cudaError_t e = cudaMalloc(&b->dmem, off);
-    if (e != cudaSuccess) return cleanup(fail(REWL_ERR_NOMEM, "cudaMalloc(%zu): %s", off, cudaGetErrorString(e)));
+    cudaError_t e = rewl::host::dev_alloc(b->dblock, off);
+    if (e != cudaSuccess)
+        return cleanup(fail(REWL_ERR_NOMEM, "device memory (%zu bytes): %s", off, cudaGetErrorString(e)));
+    b->dmem = b->dblock.ptr;
     e = cudaStreamCreateWithFlags(&b->own_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cleanup(fail(REWL_ERR_CUDA, "stream: %s", cudaGetErrorString(e)));
     b->stream = b->own_stream;
@@ -300,6 +303,7 @@ rewl_status rewl_batch_sync(rewl_batch_t b, int *n_converged) {
 }
 
 rewl_status rewl_batch_run(rewl_batch_t b, long long max_rounds, int *n_converged) {
+    const rewl::host::Range range("rewl_batch_run");
     if (!b) return fail(REWL_ERR_ARG, "NULL batch");
     const int n = (int)b->inst.size();
     int done = 0;

@@ -1,6 +1,7 @@
 // rewl_host.cu -- host driver behind include/rewl.h: parameter checks, the
 // window table, device state, the round loop as a CUDA graph, state access,
 // joining of the windows' pieces (Sec. 2, Fig. 2) and save / load.
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -232,6 +233,44 @@ struct SaveHeader {
 namespace rewl {
 namespace host {
 
+namespace {
+struct Allocator {
+    void *(*alloc)(size_t bytes, void *ctx) = nullptr;  // nullptr: cudaMalloc
+    void (*free)(void *ptr, void *ctx) = nullptr;
+    void *ctx = nullptr;
+};
+Allocator g_alloc;
+}  // namespace
+
+cudaError_t dev_alloc(DevBlock &b, size_t bytes) {
+    b = DevBlock{};
+    if (!g_alloc.alloc) return cudaMalloc(&b.ptr, bytes);
+    void *p = g_alloc.alloc(bytes, g_alloc.ctx);
+    if (!p) return cudaErrorMemoryAllocation;
+    b.ptr = p;
+    b.hooked = true;
+    b.free_fn = g_alloc.free;
+    b.ctx = g_alloc.ctx;
+    if (((uintptr_t)p & 255u) != 0) {  // the state parts are laid out at 256-byte offsets
+        dev_free(b);
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaSuccess;
+}
+
+void dev_free(DevBlock &b) {
+    if (!b.ptr) return;
+    if (!b.hooked) cudaFree(b.ptr);
+    else if (b.free_fn) b.free_fn(b.ptr, b.ctx);  // (an allocator without a free keeps its memory)
+    b = DevBlock{};
+}
+
+void set_allocator(void *(*alloc)(size_t, void *), void (*free_fn)(void *, void *), void *ctx) {
+    g_alloc.alloc = alloc;
+    g_alloc.free = alloc ? free_fn : nullptr;
+    g_alloc.ctx = alloc ? ctx : nullptr;
+}
+
 rewl_status prepare_instance(rewl_s *h, const rewl_params &p, int spin_bits, int lanes) {
     rewl_status st = check_params(p, spin_bits);
     if (st) return st;
@@ -324,6 +363,7 @@ const char *rewl_last_error(void) { return g_last_error.c_str(); }
 const char *rewl_version(void) { return "rewl-gb300 0.1 (sm_103a)"; }
 
 rewl_status rewl_create_ext(const rewl_params *prm, int spin_bits, rewl_t *out) {
+    const rewl::host::Range range("rewl_create");
     if (!prm || !out) return fail(REWL_ERR_ARG, "NULL argument");
     *out = nullptr;
     rewl_s *h = new rewl_s();
@@ -333,10 +373,10 @@ rewl_status rewl_create_ext(const rewl_params *prm, int spin_bits, rewl_t *out) 
     };
     rewl_status st = rewl::host::prepare_instance(h, *prm, spin_bits, 0);
     if (st) return cleanup(st);
-    cudaError_t e = cudaMalloc(&h->dmem, h->dbytes);
+    cudaError_t e = rewl::host::dev_alloc(h->dblock, h->dbytes);
     if (e != cudaSuccess)
-        return cleanup(fail(REWL_ERR_NOMEM, "cudaMalloc(%zu): %s", h->dbytes, cudaGetErrorString(e)));
-    rewl::host::carve_instance(h, h->dmem);
+        return cleanup(fail(REWL_ERR_NOMEM, "device memory (%zu bytes): %s", h->dbytes, cudaGetErrorString(e)));
+    rewl::host::carve_instance(h, h->dblock.ptr);
     e = cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cleanup(fail(REWL_ERR_CUDA, "stream: %s", cudaGetErrorString(e)));
     h->stream = h->own_stream;
@@ -368,13 +408,17 @@ rewl_status rewl_create(int q, int L, int h, double overlap, int m, double lnf_f
     return rewl_create_ext(&p, 0, out);
 }
 
+void rewl_set_allocator(void *(*alloc)(size_t bytes, void *ctx), void (*free_fn)(void *ptr, void *ctx), void *ctx) {
+    rewl::host::set_allocator(alloc, free_fn, ctx);
+}
+
 void rewl_destroy(rewl_t h) {
     if (!h || !h->owns) return;  // instances of a batch belong to the batch
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->graph) cudaGraphExecDestroy(h->graph);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
     if (h->h_ctl) cudaFreeHost(h->h_ctl);
-    if (h->dmem) cudaFree(h->dmem);
+    rewl::host::dev_free(h->dblock);
     delete h;
 }
 
@@ -394,6 +438,9 @@ rewl_status rewl_run_async(rewl_t h, long long rounds) {
 }
 
 rewl_status rewl_run_phase(rewl_t h, int phase) {
+    const rewl::host::Range range(phase == REWL_PHASE_SWEEP ? "rewl_phase_sweep"
+                                  : phase == REWL_PHASE_CHECK ? "rewl_phase_check"
+                                                              : "rewl_phase_exchange");
     if (h && !h->owns) return fail(REWL_ERR_STATE, "this instance belongs to a batch: run the batch");
     if (!h) return fail(REWL_ERR_ARG, "NULL handle");
     switch (phase) {
@@ -409,6 +456,11 @@ rewl_status rewl_set_option(rewl_t h, int option, long long value) {
     if (h && !h->owns) return fail(REWL_ERR_STATE, "this instance belongs to a batch: run the batch");
     if (!h) return fail(REWL_ERR_ARG, "NULL handle");
     int kind = h->plan.kind, lanes = h->plan.lanes, lat_mode = h->lat_mode;
+    if (option == REWL_OPT_STALL_MS) {  // host side only: no re-plan
+        if (value < 0) return fail(REWL_ERR_ARG, "stall limit %lld ms < 0", value);
+        h->stall_ms = value;
+        return REWL_OK;
+    }
     if (option == REWL_OPT_SWEEP_KERNEL) {
         if (value != 0 && value != 1) return fail(REWL_ERR_ARG, "sweep kernel %lld not 0 or 1", value);
         kind = value == 0 ? rewl::SWEEP_FAST : rewl::SWEEP_REFERENCE;
@@ -442,6 +494,7 @@ rewl_status rewl_get_option(rewl_t h, int option, long long *value) {
     else if (option == REWL_OPT_LANES) *value = h->plan.lanes;
     else if (option == REWL_OPT_WALKERS_PER_CTA) *value = h->plan.P;
     else if (option == REWL_OPT_LATTICE) *value = h->plan.lat_global;
+    else if (option == REWL_OPT_STALL_MS) *value = h->stall_ms;
     else return fail(REWL_ERR_ARG, "unknown option %d", option);
     return REWL_OK;
 }
@@ -454,15 +507,33 @@ rewl_status rewl_sync(rewl_t h, int *converged) {
 }
 
 rewl_status rewl_run(rewl_t h, long long max_rounds, int *converged) {
+    const rewl::host::Range range("rewl_run");
     if (h && !h->owns) return fail(REWL_ERR_STATE, "this instance belongs to a batch: run the batch");
     if (!h) return fail(REWL_ERR_ARG, "NULL handle");
     long long left = max_rounds;
     rewl_status st = read_ctl(h);
+    // stall watchdog: progress = iterations completed over all windows
+    std::vector<int32_t> iters(h->stall_ms > 0 ? (size_t)h->M.h : 0);
+    long long progress = -1;
+    auto t_progress = std::chrono::steady_clock::now();
     while (st == REWL_OK && !h->h_ctl->all_done && (max_rounds <= 0 || left > 0)) {
         const long long n = (max_rounds <= 0 || left >= kGraphRounds) ? kGraphRounds : left;
         st = enqueue_rounds(h, n);
         if (st == REWL_OK) st = read_ctl(h);
         left -= n;
+        if (st == REWL_OK && h->stall_ms > 0 && !h->h_ctl->all_done) {
+            REWL_CUDA(cudaMemcpy(iters.data(), h->S.iter, iters.size() * 4, cudaMemcpyDeviceToHost));
+            long long sum = 0;
+            for (int32_t v : iters) sum += v;
+            const auto now = std::chrono::steady_clock::now();
+            if (sum != progress) {
+                progress = sum;
+                t_progress = now;
+            } else if (std::chrono::duration_cast<std::chrono::milliseconds>(now - t_progress).count() > h->stall_ms) {
+                st = fail(REWL_ERR_TIMEOUT, "no window finished an iteration for %lld ms (round %llu)", h->stall_ms,
+                          (unsigned long long)h->h_ctl->round);
+            }
+        }
     }
     if (converged) *converged = h->h_ctl->all_done ? 1 : 0;
     return st;

@@ -3,8 +3,36 @@
 #pragma once
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "rewl.h"
 #include "rewl_internal.cuh"
+
+namespace rewl {
+namespace host {
+
+// Device memory of a handle, a batch or a server: from the allocator set with
+// rewl_set_allocator (else cudaMalloc), returned through the matching free.
+struct DevBlock {
+    void *ptr = nullptr;
+    bool hooked = false;                              // false: cudaMalloc / cudaFree
+    void (*free_fn)(void *ptr, void *ctx) = nullptr;  // hooked: nullptr means kept by the allocator
+    void *ctx = nullptr;
+};
+// cudaSuccess, or cudaErrorMemoryAllocation (also for memory not 256-byte aligned).
+cudaError_t dev_alloc(DevBlock &b, size_t bytes);
+void dev_free(DevBlock &b);
+void set_allocator(void *(*alloc)(size_t, void *), void (*free_fn)(void *, void *), void *ctx);
+
+// A named range on the host timeline of a profiler (NVTX; free when none is attached).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
+}  // namespace host
+}  // namespace rewl
 
 struct rewl_s {
     rewl_params prm{};
@@ -15,12 +43,14 @@ struct rewl_s {
     cudaStream_t own_stream = nullptr;
     cudaStream_t stream = nullptr;
     void *dmem = nullptr;  // base of this instance's device arrays
+    rewl::host::DevBlock dblock;  // the allocation behind dmem (stand-alone handles)
     size_t dbytes = 0;
     rewl::Ctl *h_ctl = nullptr;  // pinned mirror of the device control block
     std::vector<int32_t> e_lo;
     cudaGraphExec_t graph = nullptr;
     int sms = 0, smem_optin = 0;
     int lat_mode = 0;  // REWL_OPT_LATTICE: 0 by size, 1 global memory, 2 shared memory
+    long long stall_ms = 0;  // REWL_OPT_STALL_MS: rewl_run gives up after this long without progress
     // byte offsets of the state arrays relative to dmem (for save / load); the
     // last part is the control block
     struct Part { size_t off, bytes; };
@@ -32,6 +62,7 @@ struct rewl_s {
 
 namespace rewl {
 namespace host {
+
 
 // Checks the parameters, computes the window table and the sizes of the device
 // arrays (h->parts, h->dbytes) and plans the sweep.  lanes: lanes per walker of

@@ -98,6 +98,7 @@ double now_s() {
 
 struct rewl_server_s {
     void *arena_mem = nullptr;
+    rewl::host::DevBlock arena_block, ctl_block, tab_block;  // the device allocations
     Arena arena;
     int max_jobs = 0;
     rewl::Ctl *d_ctls = nullptr;  // [max_jobs] control blocks (one per slot)
@@ -173,10 +174,11 @@ rewl_status rebuild_tables(rewl_server_s *s) {
                         align256(s->cls[1].items.size() * sizeof(rewl::SweepItem) + 16) + 256;
     if (need > s->tab_cap) {
         SRV_CUDA(cudaStreamSynchronize(s->stream));
-        if (s->d_tab) cudaFree(s->d_tab);
+        rewl::host::dev_free(s->tab_block);
         s->d_tab = nullptr;
         s->tab_cap = std::max(need * 2, (size_t)(64 << 10));
-        SRV_CUDA(cudaMalloc(&s->d_tab, s->tab_cap));
+        SRV_CUDA(rewl::host::dev_alloc(s->tab_block, s->tab_cap));
+        s->d_tab = s->tab_block.ptr;
     }
     char *p = (char *)s->d_tab;
     s->d_inst = (rewl::InstDev *)p;
@@ -282,10 +284,13 @@ rewl_status rewl_server_create(size_t pool_bytes, int max_jobs, rewl_server_t *o
     cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&s->optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     pool_bytes = align256(pool_bytes);
-    cudaError_t e = cudaMalloc(&s->arena_mem, pool_bytes);
-    if (e != cudaSuccess) return cleanup(fail(REWL_ERR_NOMEM, "cudaMalloc(%zu): %s", pool_bytes, cudaGetErrorString(e)));
+    cudaError_t e = rewl::host::dev_alloc(s->arena_block, pool_bytes);
+    if (e != cudaSuccess)
+        return cleanup(fail(REWL_ERR_NOMEM, "device pool (%zu bytes): %s", pool_bytes, cudaGetErrorString(e)));
+    s->arena_mem = s->arena_block.ptr;
     s->arena.reset(pool_bytes);
-    e = cudaMalloc(&s->d_ctls, sizeof(rewl::Ctl) * (size_t)max_jobs);
+    e = rewl::host::dev_alloc(s->ctl_block, sizeof(rewl::Ctl) * (size_t)max_jobs);
+    s->d_ctls = (rewl::Ctl *)s->ctl_block.ptr;
     if (e == cudaSuccess) e = cudaMallocHost(&s->h_ctls, sizeof(rewl::Ctl) * (size_t)max_jobs);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cleanup(fail(REWL_ERR_NOMEM, "server set-up: %s", cudaGetErrorString(e)));
@@ -299,10 +304,10 @@ void rewl_server_destroy(rewl_server_t s) {
     if (s->stream) cudaStreamSynchronize(s->stream);
     for (auto &kv : s->jobs)
         if (kv.second.inst) delete kv.second.inst;
-    if (s->d_tab) cudaFree(s->d_tab);
-    if (s->d_ctls) cudaFree(s->d_ctls);
+    rewl::host::dev_free(s->tab_block);
+    rewl::host::dev_free(s->ctl_block);
     if (s->h_ctls) cudaFreeHost(s->h_ctls);
-    if (s->arena_mem) cudaFree(s->arena_mem);
+    rewl::host::dev_free(s->arena_block);
     if (s->stream) cudaStreamDestroy(s->stream);
     delete s;
 }
@@ -326,6 +331,7 @@ rewl_status rewl_server_submit(rewl_server_t s, const rewl_params *p, int spin_b
 }
 
 rewl_status rewl_server_step(rewl_server_t s, long long rounds, int *n_running, int *n_queued) {
+    const rewl::host::Range range("rewl_server_step");
     if (!s) return fail(REWL_ERR_ARG, "NULL server");
     if (rounds < 1) return fail(REWL_ERR_ARG, "rounds < 1");
     rewl_status st = admit(s);

@@ -28,6 +28,26 @@ def _ptr(a):
     return a.ctypes.data_as(C.c_void_p)
 
 
+_allocator_refs = None  # keeps the callbacks alive while the library may call them
+
+
+def set_allocator(alloc=None, free=None):
+    """Device memory for the handles, batches and servers created from now on:
+    alloc(nbytes) -> device pointer (int, 256-byte aligned) or 0; free(ptr).
+    set_allocator() restores cudaMalloc.  Objects free through the allocator
+    that gave them their memory."""
+    global _allocator_refs
+    L = _lib.load()
+    if alloc is None:
+        L.rewl_set_allocator(_lib.ALLOC_FN(), _lib.FREE_FN(), None)
+        return
+    a = _lib.ALLOC_FN(lambda n, ctx: alloc(n) or None)
+    f = _lib.FREE_FN((lambda p, ctx: free(p)) if free else (lambda p, ctx: None))
+    old = _allocator_refs
+    _allocator_refs = (a, f, old)  # earlier callbacks stay alive for the objects that use them
+    L.rewl_set_allocator(a, f, None)
+
+
 class REWL:
     """One REWL instance on the current CUDA device.
 
