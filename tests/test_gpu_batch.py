@@ -101,3 +101,24 @@ def test_generated_batch_workload_builds():
     assert info["walkers"] == sum(j["h"] * j["m"] for j in jobs)
     b.run(2)
     assert b.stats()["flips"] == 2 * sum(j["h"] * j["m"] * j["exchange_interval"] for j in jobs)
+
+
+def test_full_batched_workload_sampled_instances_match_the_oracle():
+    """The full 2048-instance batch in the configuration the benchmark times
+    (a thread per walker, 56,784 walkers): a sample of instances, each
+    recomputed alone by the oracle, agrees bit for bit after two rounds."""
+    jobs = WL.batched_instances(2048)
+    b = Batch(jobs)
+    assert b.info()["walkers"] >= 16384  # the thread-per-walker mapping
+    b.run(2)
+    rng = np.random.default_rng(11)
+    for i in rng.choice(len(jobs), 6, replace=False):
+        j = jobs[int(i)]
+        orc = O.OracleREWL(*WL.rewl_args(j, j["seed"]))
+        orc.run(2)
+        v = b.instance(int(i))
+        assert np.array_equal(v.get("spins"), orc.sigma()), i
+        assert np.array_equal(v.get("lng").view(np.uint64), orc.lng().view(np.uint64)), i
+        assert np.array_equal(v.get("hist"), orc.H()), i
+        assert np.array_equal(v.get("replica"), orc.rep()), i
+        assert np.array_equal(v.get("trips"), orc.rt_trips()), i

@@ -283,3 +283,33 @@ def test_many_walkers_run_a_thread_each_with_global_state():
     for n in (1, 2):
         run_both(gpu, orc, n)
         assert_parity(gpu, orc)
+
+
+def test_paper_size_workload_invariants():
+    """q=10, L=300, 717 windows x 3 walkers (2151 walkers, 45 KB lattices in
+    global memory), one round in the benchmark's configuration; too big for
+    the oracle's window entry, so checked by what holds at any size: every
+    energy is the recount of its lattice and lies in its walker's window, and
+    with ln f = 1 and no merge yet, ln g equals the visit histogram bin by bin
+    and both sum to K per walker."""
+    from paper_1312_3004_gb300 import _lib
+    p = WL.params("potts10_L300")
+    r = REWL(*WL.rewl_args(p, 1), spin_bits=p["spin_bits"])
+    assert r.get_option(_lib.OPT_LATTICE) == 1
+    r.run(1)
+    K = p["exchange_interval"]
+    H = r.get("hist")
+    lng = r.get("lng")
+    assert np.array_equal(H.sum(axis=1), np.full(r.G, K))
+    assert np.array_equal(lng, H.astype(np.float64))
+    assert np.array_equal(r.get("steps"), np.full(r.G, K, dtype=np.uint64))
+    E = r.get("energy")
+    e_lo = r.get("e_lo")
+    w = np.arange(r.G) // p["m"]
+    assert np.all(E >= e_lo[w]) and np.all(E <= e_lo[w] + r.W)
+    spins = r.get("spins")
+    L = p["L"]
+    for g in np.random.default_rng(3).choice(r.G, 24, replace=False):
+        s = spins[g].reshape(L, L).astype(np.int32)
+        recount = -int((s == np.roll(s, -1, axis=1)).sum() + (s == np.roll(s, -1, axis=0)).sum())
+        assert recount == E[g], g
