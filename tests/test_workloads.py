@@ -1,0 +1,40 @@
+"""The seeded synthetic inputs: the named configurations, the batched
+instances and the serving trace are reproducible and have the stated shapes."""
+import numpy as np
+
+from paper_1312_3004_gb300 import workloads as WL
+
+
+def test_named_configurations():
+    p = WL.params("potts10_L80")
+    assert (p["q"], p["L"], p["h"], p["m"]) == (10, 80, 64, 16)
+    assert WL.rewl_args(p, 7)[-1] == 7
+    paper = WL.params("potts10_L300")
+    assert (paper["L"], paper["h"], paper["m"], paper["overlap"]) == (300, 717, 3, 0.75)
+    assert WL.params("ising_L8", m=4)["m"] == 4  # overrides
+
+
+def test_batched_instances_are_reproducible_and_in_range():
+    a = WL.batched_instances(2048)
+    b = WL.batched_instances(2048)
+    assert a == b
+    assert len(a) == 2048
+    assert {j["q"] for j in a} <= {2, 4, 8, 10}
+    assert {j["L"] for j in a} <= set(range(8, 49, 4))
+    assert {j["h"] for j in a} <= {4, 8, 16} and {j["m"] for j in a} <= {2, 4}
+    assert len({j["seed"] for j in a}) == 2048
+    walkers = sum(j["h"] * j["m"] for j in a)
+    assert 40000 < walkers < 80000
+    assert WL.batched_instances(16, master_seed=1) != WL.batched_instances(16, master_seed=2)
+
+
+def test_serving_trace_is_a_poisson_stream():
+    tr = WL.serving_trace(n=2000)
+    assert tr == WL.serving_trace(n=2000)
+    t = np.array([x[0] for x in tr])
+    assert np.all(np.diff(t) > 0)
+    gaps = np.diff(np.concatenate([[0.0], t]))
+    assert abs(gaps.mean() - 1 / 50.0) < 0.002  # mean gap 20 ms
+    assert abs(gaps.std() / gaps.mean() - 1.0) < 0.1  # exponential: coefficient of variation 1
+    for _, j in tr[:200]:
+        assert 2 <= j["q"] <= 10 and 6 <= j["L"] <= 12 and 2 <= j["h"] <= 6 and 2 <= j["m"] <= 4
