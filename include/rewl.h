@@ -241,8 +241,10 @@ rewl_status rewl_load(rewl_t h, const void *buf, size_t len);
 
 /* ---- Batches: many independent instances advanced together -----------------
  * A batch holds n instances of uneven (q, L, h, m) in one device allocation.
- * Each round runs one persistent sweep launch that takes walker groups of
- * every unfinished instance from a device queue, one batched check launch
+ * Each round runs one sweep launch per spin packing -- a persistent launch
+ * that takes walker groups of every unfinished instance from a device queue
+ * (lane groups), or one thread per walker of every instance (see
+ * rewl_batch_create_ext) -- then one batched check launch
  * (every window of every instance) and one batched exchange launch; rounds
  * are replayed as a CUDA graph.  Every instance computes exactly the states it
  * computes alone (same parameters, same seed): batching changes the runtime,
