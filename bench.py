@@ -43,6 +43,9 @@ ALG_FP64_PER_FLIP = 2  # D = ln g(E) - ln g(E'), ln g(E) += ln f
 SMS = 152
 LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
+# DRAM bytes (read + write) of one sweep launch, from ncu captures of the
+# current kernels (profiles/sweep_fast_potts10_L80.md, profiles/batch_walker_batched2048.md)
+TRAFFIC_PER_LAUNCH = {"potts10_L80": 10.05e6, "batched2048": 6.40e9}
 
 
 def parse_args():
@@ -313,7 +316,7 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": dict(config_of(args.workload, p), parallelism="replicas" if world > 1 else "single"),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH.get(args.workload),
                      "kernel": "sweep_kernel", "avg_launch_ms": sweep_avg_s * 1e3,
                      "ops_per_flip": ALG_OPS_PER_FLIP,
                      "peak_basis": "152 SMs x 128 INT32/FP32 lanes x 2070 MHz (recipe unit counts)",
@@ -411,7 +414,7 @@ def run_batched(args):
             "roofline": {"bound": "alu", "achieved": value * ALG_OPS_PER_FLIP / 1e12,
                          "peak": SMS * LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12, "unit": "Tops/s",
                          "frac": value * ALG_OPS_PER_FLIP / (SMS * LANES_PER_SM * SM_MAX_MHZ * 1e6),
-                         "traffic": None, "ops_per_flip": ALG_OPS_PER_FLIP},
+                         "traffic": TRAFFIC_PER_LAUNCH["batched2048"], "ops_per_flip": ALG_OPS_PER_FLIP},
             "lane_groups": {"value": groups, "unit": "flips/s",
                             "form": "32 lanes per walker, state staged in shared memory"}}
     print(json.dumps(line), flush=True)
