@@ -45,7 +45,7 @@ LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 # DRAM bytes (read + write) of one sweep launch, from ncu captures of the
 # current kernels (profiles/sweep_fast_potts10_L80.md, profiles/batch_walker_batched2048.md)
-TRAFFIC_PER_LAUNCH = {"potts10_L80": 10.05e6, "batched2048": 6.40e9}
+TRAFFIC_PER_LAUNCH = {"potts10_L80": 10.19e6, "batched2048": 6.40e9}
 
 
 def parse_args():
