@@ -118,3 +118,30 @@ def test_static_run_rejects_bad_parameters_before_any_device_work(kw):
     conv = C.c_int(-1)
     assert lib.rewl_run_static(C.byref(p), 0, 1, buf, None, 16, C.byref(conv), None) == 1
     assert lib.rewl_run_static(None, 0, 1, buf, None, 16, C.byref(conv), None) == 1
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/rewl.h compiles as C99 (no C++ or CUDA types cross the ABI) and a
+    C program that links the library's symbols type-checks against it."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use.c"
+    src.write_text('''#include "rewl.h"
+#include <stddef.h>
+int main(void) {
+    rewl_t h = NULL;
+    int conv = 0;
+    rewl_params p = {10, 8, 4, 0.75, 2, 1e-6, 0.8, 1000, 1ull};
+    if (rewl_create_ext(&p, 0, &h) != REWL_OK) return 1;
+    rewl_run(h, 0, &conv);
+    rewl_set_allocator(NULL, NULL, NULL);
+    rewl_destroy(h);
+    return rewl_last_error()[0] != 0;
+}
+''')
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-pedantic", "-fsyntax-only", "-I",
+                        os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
