@@ -94,10 +94,44 @@ def reduce_over_ranks(dist, device, total_ms, flips, e2e_flips_per_s):
 
 
 # ---------------------------------------------------------------------------
-class ClockSampler:
-    """nvidia-smi samples every 200 ms during the timed region."""
+def summarize_clocks(lines, uuid=None, t0=None, t1=None):
+    """The clock record of a timed region from nvidia-smi CSV rows
+    (timestamp, index, uuid, clocks.sm, clocks.max.sm, power, active reasons,
+    hw_slowdown, hw_thermal_slowdown, sw_thermal_slowdown, sw_power_cap):
+    median SM clock under load, its maximum, and every throttle reason seen.
+    Rows outside [t0, t1] (epoch seconds) are left out when the region holds
+    any."""
+    import datetime
 
-    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    rows = []
+    for line in lines:
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 11 or (uuid and parts[2] != uuid):
+            continue
+        try:
+            ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            ts = None
+        rows.append((ts, parts[1:]))
+    if t0 is not None and t1 is not None:
+        inside = [r for r in rows if r[0] is not None and t0 <= r[0] <= t1]
+        if inside:
+            rows = inside
+    rows = [r for _, r in rows]
+    if not rows:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+    sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+    mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i].lower() == "active"})
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+            "reasons": reasons, "samples": len(rows)}
+
+
+class ClockSampler:
+    """nvidia-smi samples every 100 ms around the timed region."""
+
+    FIELDS = ("timestamp,index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -111,12 +145,13 @@ class ClockSampler:
         os.close(fd)
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"],
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
 
-    def stop(self):
+    def stop(self, t0=None, t1=None):
+        """Stop sampling; the record of the samples taken in [t0, t1] (epoch s)."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -124,23 +159,10 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        rows = []
-        for line in open(self.path):
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 10:
-                continue
-            if self.uuid and parts[1] != self.uuid:
-                continue
-            rows.append(parts)
+        with open(self.path) as f:
+            lines = f.readlines()
         os.unlink(self.path)
-        if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
-        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i].lower() == "active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+        return summarize_clocks(lines, self.uuid, t0, t1)
 
 
 # ---------------------------------------------------------------------------
@@ -271,6 +293,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     sampler.start()
     time.sleep(0.3)
+    epoch0 = time.time()
     wall0 = time.perf_counter()
     for i in range(args.steps):
         with torch.cuda.stream(stream):
@@ -278,7 +301,7 @@ def run_ours(args):
         one_step(events[i])
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
-    clocks = sampler.stop()
+    clocks = sampler.stop(epoch0, time.time())
     s1 = r.stats()
     step_ms = [a.elapsed_time(c) for a, _, c in events]
     sweep_ms = [a.elapsed_time(b) for a, b, _ in events]

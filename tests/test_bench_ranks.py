@@ -65,3 +65,28 @@ def test_reference_arm_runs_on_rank_zero_only():
                         "--warmup", "0"], env=env, capture_output=True, text=True, timeout=120)
     assert p.returncode == 0, p.stderr
     assert p.stdout.strip() == ""
+
+
+def test_clock_record_keeps_the_timed_region_and_every_throttle_reason():
+    sys.path.insert(0, ROOT)
+    import datetime
+
+    import bench
+
+    def row(t, sm, reasons=("Not Active",) * 4, uuid="GPU-a"):
+        ts = datetime.datetime.fromtimestamp(t).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+        return ", ".join([ts, "0", uuid, str(sm), "2070", "900.0", "0x0"] + list(reasons))
+
+    t0 = 1_800_000_000.0
+    lines = [row(t0 - 0.5, 1000),  # before the region: idle clock, left out
+             row(t0 + 0.1, 2070), row(t0 + 0.3, 2070),
+             row(t0 + 0.5, 1800, ("Not Active", "Not Active", "Not Active", "Active")),
+             row(t0 + 0.6, 2000, uuid="GPU-b"),  # another GPU
+             row(t0 + 2.0, 500)]  # after the region
+    rec = bench.summarize_clocks(lines, "GPU-a", t0, t0 + 1.0)
+    assert rec["samples"] == 3
+    assert rec["sm_mhz"] == 2070.0 and rec["sm_max_mhz"] == 2070.0
+    assert rec["reasons"] == ["sw_power_cap"]
+    hot = bench.summarize_clocks([row(t0, 1500, ("Active", "Not Active", "Not Active", "Not Active"))], None)
+    assert hot["reasons"] == ["hw_slowdown"]
+    assert bench.summarize_clocks([], None)["reasons"] == ["no samples"]
