@@ -112,7 +112,8 @@ rewl_status rewl_create(int q, int L, int h, double overlap, int m, double lnf_f
 rewl_status rewl_create_ext(const rewl_params *params, int spin_bits, rewl_t *out);
 
 /* Queue subsequent work of the handle on `stream` (a cudaStream_t passed as
- * void*; NULL selects the handle's own stream).  The stream must belong to the
+ * void*; NULL selects the handle's own stream).  Runtime plumbing with no
+ * counterpart in the paper.  The stream must belong to the
  * handle's device and outlive its use by the handle. */
 rewl_status rewl_set_stream(rewl_t h, void *stream);
 
@@ -126,12 +127,13 @@ rewl_status rewl_set_stream(rewl_t h, void *stream);
  * done.  Errors: REWL_ERR_OVERFLOW, REWL_ERR_CUDA, REWL_ERR_ARG. */
 rewl_status rewl_run(rewl_t h, long long max_rounds, int *converged);
 
-/* Queue exactly `rounds` exchange rounds on the handle's stream and return
- * without synchronising (for timing with events on that stream).  Status
+/* Queue exactly `rounds` exchange rounds (Sec. 2, as rewl_run) on the handle's
+ * stream and return without synchronising (for timing with events on that
+ * stream).  Status
  * flags are checked by the next synchronising call. */
 rewl_status rewl_run_async(rewl_t h, long long rounds);
 
-/* Queue one phase of an exchange round on the handle's stream without
+/* Queue one phase of an exchange round (Sec. 2) on the handle's stream without
  * synchronising: REWL_PHASE_SWEEP (K WL steps of every walker of every
  * unfinished window), REWL_PHASE_CHECK (mask, flatness, merge, f-reduction),
  * REWL_PHASE_EXCHANGE (replica exchange, then round + 1).  A round is the
@@ -141,8 +143,8 @@ rewl_status rewl_run_async(rewl_t h, long long rounds);
 enum { REWL_PHASE_SWEEP = 0, REWL_PHASE_CHECK = 1, REWL_PHASE_EXCHANGE = 2 };
 rewl_status rewl_run_phase(rewl_t h, int phase);
 
-/* Tuning options of a handle (no effect on results: every choice computes
- * the same states bit for bit):
+/* Tuning options of a handle (no counterpart in the paper, and no effect on
+ * results: every choice computes the same states bit for bit):
  *   REWL_OPT_SWEEP_KERNEL  0 = fast sweep (integer acceptance path with a
  *                          binary64 fallback), 1 = binary64 reference sweep
  *   REWL_OPT_LANES         lanes per walker of the fast sweep: 0 = chosen from
@@ -174,7 +176,8 @@ rewl_status rewl_set_option(rewl_t h, int option, long long value);
 rewl_status rewl_get_option(rewl_t h, int option, long long *value);
 
 /* Synchronise the handle's stream and report its device status:
- * *converged (may be NULL) as in rewl_run. */
+ * *converged (may be NULL) as in rewl_run (Sec. 2's global termination: every
+ * window below f_final).  Errors: REWL_ERR_OVERFLOW, REWL_ERR_CUDA. */
 rewl_status rewl_sync(rewl_t h, int *converged);
 
 /* The joined, normalised ln g over all 2N + 1 bins (Sec. 2, Fig. 2): for each
@@ -187,16 +190,25 @@ rewl_status rewl_sync(rewl_t h, int *converged);
 rewl_status rewl_get_lng(rewl_t h, double *out, size_t len, int partial);
 
 /* ln g of window w as held by its walker 0 (W + 1 doubles into `out`, host),
- * and the window's lowest energy in *e_lo (may be NULL). */
+ * and the window's lowest energy in *e_lo (may be NULL).  After a merge every
+ * walker of the window holds the same average (Sec. 2), so walker 0 stands for
+ * the window; unjoined and unnormalised (Fig. 2 before the join).
+ * Errors: REWL_ERR_ARG (w outside [0, h), len != W + 1). */
 rewl_status rewl_get_window_lng(rewl_t h, int w, double *out, size_t len, int *e_lo);
 
-/* Sizes of the instance. */
+/* Sizes of the instance (W from the window formula of Sec. 2 / Fig. 1). */
 rewl_status rewl_get_info(rewl_t h, rewl_info *info);
 
-/* Counters of the instance (synchronises the stream). */
+/* Counters of the instance (synchronises the stream): WL proposals and
+ * acceptances (Sec. 2's single-spin-flip steps, Sec. 3.1), Eq. 1 exchange
+ * trials and acceptances, windows done; the fast-sweep counters describe the
+ * implementation, not the method. */
 rewl_status rewl_get_stats(rewl_t h, rewl_stats *stats);
 
-/* Copy one state array of the instance to host memory (synchronises):
+/* Copy one state array of the instance to host memory (synchronises).  The
+ * arrays are Sec. 2's per-walker state (configuration, E, ln g(E), H(E)) and
+ * per-window state (ln f, iterations); the replica ids and round-trip counters
+ * follow the replica paths through the windows that Fig. 7 plots:
  *   REWL_FIELD_SPINS  uint8  [h*m][N]  configuration held by walker g = i*m + k
  *   REWL_FIELD_ENERGY int32  [h*m]     its energy
  *   REWL_FIELD_REPLICA uint32 [h*m]    its replica id (initially g)
@@ -231,7 +243,8 @@ rewl_status rewl_get_field(rewl_t h, int field, void *out, size_t bytes);
  * state, e.g. fixed weights with ln f = 0. */
 rewl_status rewl_set_field(rewl_t h, int field, const void *in, size_t bytes);
 
-/* Serialise the whole state (at a round boundary) into `buf` (host).  With
+/* Checkpoint and resume (no counterpart in the paper).
+ * Serialise the whole state (at a round boundary) into `buf` (host).  With
  * buf == NULL only *len is set to the required size.  rewl_load restores it
  * into a handle created with the same parameters; run(2K) equals
  * run(K) + save + load + run(K) bit for bit.  Errors: REWL_ERR_ARG (buffer too
@@ -375,10 +388,11 @@ void rewl_destroy(rewl_t h);
  * misaligned pointer) makes the creating call fail with REWL_ERR_NOMEM. */
 void rewl_set_allocator(void *(*alloc)(size_t bytes, void *ctx), void (*free)(void *ptr, void *ctx), void *ctx);
 
-/* Message of the last error on this thread ("" if none). */
+/* Message of the last error on this thread ("" if none).  No counterpart in
+ * the paper. */
 const char *rewl_last_error(void);
 
-/* Library version string. */
+/* Library version string.  No counterpart in the paper. */
 const char *rewl_version(void);
 
 #ifdef __cplusplus
