@@ -377,6 +377,70 @@ rewl_status rewl_run_static(const rewl_params *params, int spin_bits, long long 
 /* Release the handle and its device memory.  NULL is ignored. */
 void rewl_destroy(rewl_t h);
 
+/* ---- Analysis of a density of states (host functions, no device work) -------
+ * Each takes a joined ln g as rewl_get_lng returns it: lng[b] = ln g(E) for
+ * E = b - 2N, b = 0 .. 2N (len = 2N + 1, so N = (len - 1) / 2), -INFINITY for
+ * energies without configurations; NaN or +inf entries and an array without a
+ * finite entry are REWL_ERR_ARG.  Temperatures are in units of J / k_B and must
+ * be finite and > 0.  All arrays are caller-owned host memory. */
+
+/* Canonical averages per spin (Sec. 3.1: the canonical distribution
+ * P(E) ~ g(E) exp(-E/T) of Fig. 3b and its moments) at the nT temperatures
+ * T[0 .. nT-1]: out[4i + 0] = u = <E> / N, out[4i + 1] = c = (<E^2> - <E>^2) /
+ * (N T^2), out[4i + 2] = f = -T ln Z / N, out[4i + 3] = s = (u - f) / T, with
+ * Z = sum_E g(E) exp(-E/T).  out holds 4 nT doubles. */
+rewl_status rewl_canonical(const double *lng, size_t len, const double *T, size_t nT, double *out);
+
+/* The canonical distribution at T scaled to 1 at its highest point (Fig. 3b
+ * shows it normalised to 1 at the peaks): out[b] = P(E) / max P, 0 where
+ * lng[b] = -INFINITY.  out holds len doubles. */
+rewl_status rewl_canonical_distribution(const double *lng, size_t len, double T, double *out);
+
+/* The largest specific heat c(T) (as rewl_canonical) for T in [T_lo, T_hi]:
+ * a scan of 1025 temperatures, then a golden-section search between the best
+ * one's neighbours down to 1e-13 T_hi.  *T_peak, *c_peak receive the maximum.
+ * Errors: REWL_ERR_ARG (T_lo <= 0, T_hi <= T_lo, NULL output). */
+rewl_status rewl_specific_heat_peak(const double *lng, size_t len, double T_lo, double T_hi, double *T_peak,
+                                    double *c_peak);
+
+/* The finite-size transition temperature Tc(L) of a first-order transition
+ * (Sec. 3.1: 0.70126 for q = 10, L = 300; Fig. 3b): the temperature at which
+ * the canonical distribution has two maxima of equal height.  Such pairs are
+ * the successive vertices of the upper concave hull of (E, ln g(E)), at
+ * T = 1 / slope of the edge between them; of the edges with T in
+ * [T_lo, T_hi] the one spanning the widest energy range is taken (ties: the
+ * lower one).  *Tc receives T; *e_low, *e_high (may be NULL) the energies of
+ * the two peaks; *ln_suppression (may be NULL) ln of the smallest P(E) / P(peak)
+ * between them (about ln 1e-14 for L = 300, Sec. 3.1).  Errors: REWL_ERR_STATE
+ * when no edge has its temperature in the range. */
+rewl_status rewl_equal_peak_temperature(const double *lng, size_t len, double T_lo, double T_hi, double *Tc,
+                                        int *e_low, int *e_high, double *ln_suppression);
+
+/* Join window pieces supplied by the caller into one normalised ln g: the
+ * step rewl_get_lng applies to a run's own windows (Sec. 2, Fig. 2: each
+ * neighbouring pair meets at the bin of their overlap where the pieces' slopes
+ * d ln g / dE differ least; sum g = q^N).  e_lo[h]: lowest energy of each
+ * window (increasing, inside [-2N, 0] with W); lng_w, mask_w: h x (W + 1),
+ * window-major, mask 1 where the bin was visited; out: len = 2N + 1 doubles,
+ * N = L * L.  Errors: REWL_ERR_ARG, REWL_ERR_STATE (a pair without a usable
+ * joining bin). */
+rewl_status rewl_join(int q, int L, int h, int W, const int *e_lo, const double *lng_w, const unsigned char *mask_w,
+                      double *out, size_t len);
+
+/* Bootstrap resampling of repeated runs (end of Sec. 2: the simulation is
+ * repeated and resampled, and every resampled density of states is joined
+ * anew, so its joining points move).  lng_runs, mask_runs: runs x h x (W + 1)
+ * window pieces of `runs` runs of one geometry (e.g. rewl_get_field's
+ * REWL_FIELD_LNG rows of walker 0 of every window, and REWL_FIELD_MASK).
+ * Resample k takes the runs draws[k * runs .. k * runs + runs - 1] (indices in
+ * [0, runs), drawn by the caller, repeats allowed), averages their pieces bin
+ * by bin over the drawn runs that visited the bin (mask: visited by any), and
+ * joins and normalises the averages as rewl_join into out[k * len .. ].  out
+ * holds resamples x len doubles.  Errors as rewl_join, and REWL_ERR_ARG for a
+ * draw outside [0, runs). */
+rewl_status rewl_bootstrap(int q, int L, int h, int W, const int *e_lo, int runs, const double *lng_runs,
+                           const unsigned char *mask_runs, int resamples, const int *draws, double *out, size_t len);
+
 /* Device memory source for the handles, batches and servers created from now
  * on (no counterpart in the paper: it lets a framework's caching allocator, or
  * a fixed budget, supply the state arrays).  alloc(bytes, ctx) returns device

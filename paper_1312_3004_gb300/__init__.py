@@ -6,6 +6,8 @@ The computation runs in the CUDA library behind include/rewl.h
 only marshals arguments.
 """
 from ._lib import RewlError, load  # noqa: F401
-from .rewl import REWL, Batch, Server  # noqa: F401
+from .rewl import (REWL, Batch, Server, bootstrap, canonical, canonical_distribution,  # noqa: F401
+                   equal_peak_temperature, join, specific_heat_peak)
 
-__all__ = ["REWL", "Batch", "Server", "RewlError", "load"]
+__all__ = ["REWL", "Batch", "Server", "RewlError", "load", "canonical", "canonical_distribution",
+           "specific_heat_peak", "equal_peak_temperature", "join", "bootstrap"]

@@ -118,6 +118,17 @@ def load():
     L.rewl_batch_destroy.restype = None
     L.rewl_destroy.argtypes = [H]
     L.rewl_destroy.restype = None
+    pi = C.POINTER(C.c_int)
+    pd = C.POINTER(C.c_double)
+    L.rewl_canonical.argtypes = [vp, sz, vp, sz, vp]
+    L.rewl_canonical_distribution.argtypes = [vp, sz, C.c_double, vp]
+    L.rewl_specific_heat_peak.argtypes = [vp, sz, C.c_double, C.c_double, pd, pd]
+    L.rewl_equal_peak_temperature.argtypes = [vp, sz, C.c_double, C.c_double, pd, pi, pi, pd]
+    L.rewl_join.argtypes = [i32, i32, i32, i32, vp, vp, vp, vp, sz]
+    L.rewl_bootstrap.argtypes = [i32, i32, i32, i32, vp, i32, vp, vp, i32, vp, vp, sz]
+    for name in ("rewl_canonical", "rewl_canonical_distribution", "rewl_specific_heat_peak",
+                 "rewl_equal_peak_temperature", "rewl_join", "rewl_bootstrap"):
+        getattr(L, name).restype = st
     L.rewl_last_error.argtypes = []
     L.rewl_last_error.restype = C.c_char_p
     L.rewl_version.argtypes = []

@@ -13,7 +13,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "librewl.so")
-SOURCES = ["rewl_kernels.cu", "rewl_sweep.cu", "rewl_host.cu", "rewl_batch.cu", "rewl_server.cu", "rewl_static.cu"]
+SOURCES = ["rewl_kernels.cu", "rewl_sweep.cu", "rewl_host.cu", "rewl_batch.cu", "rewl_server.cu", "rewl_static.cu",
+           "rewl_analysis.cu"]
 HEADERS = ["rewl_internal.cuh", "rewl_host_internal.hpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

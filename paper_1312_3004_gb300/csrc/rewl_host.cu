@@ -140,7 +140,12 @@ rewl_status read_ctl(rewl_s *h) {
     return REWL_OK;
 }
 
+}  // namespace
+
 // ---- joining (Sec. 2, Fig. 2) ------------------------------------------------
+namespace rewl {
+namespace host {
+
 // Slope of a piece at local bin i: difference quotient between the nearest
 // visited bins below and above i (i itself must be visited).
 bool piece_slope(const double *lg, const uint8_t *vis, int B, int i, double *beta) {
@@ -203,6 +208,14 @@ void normalise_total(int q, int N, double *v, int nb) {
     for (int b = 0; b < nb; ++b)
         if (v[b] != -INFINITY) v[b] += shift;
 }
+
+}  // namespace host
+}  // namespace rewl
+
+using rewl::host::join_windows;
+using rewl::host::normalise_total;
+
+namespace {
 
 uint64_t fnv1a(const unsigned char *p, size_t n, uint64_t hsh = 1469598103934665603ull) {
     for (size_t i = 0; i < n; ++i) {

@@ -75,6 +75,14 @@ cudaError_t init_instance_async(rewl_s *h, cudaStream_t s);
 // Reads the control block (synchronises h->stream) and maps its error bits.
 rewl_status read_status(rewl_s *h);
 rewl_status fail(rewl_status st, const char *fmt, ...);
+// Joins h window pieces (lw, mw: h x (W + 1), window-major) into out[2N + 1]
+// (Sec. 2, Fig. 2): each neighbouring pair meets at the bin of their overlap
+// where the pieces' slopes d ln g / dE differ least; -inf where no window
+// visited a bin.  REWL_ERR_STATE when a pair has no usable bin.
+rewl_status join_windows(int N, int W, const std::vector<int32_t> &e_lo, const std::vector<double> &lw,
+                         const std::vector<uint8_t> &mw, double *out);
+// Shifts the finite entries of v[nb] so that sum g = q^N.
+void normalise_total(int q, int N, double *v, int nb);
 
 }  // namespace host
 }  // namespace rewl

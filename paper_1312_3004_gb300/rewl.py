@@ -122,6 +122,11 @@ class REWL:
         check(self._L.rewl_get_lng(self._h, _ptr(out), out.size, 1 if partial else 0))
         return out
 
+    def window_pieces(self):
+        """(e_lo[h], W, ln g[h][W+1] of walker 0 of each window, mask[h][W+1]):
+        the pieces rewl_join / rewl_bootstrap take."""
+        return self.get("e_lo"), self.W, np.ascontiguousarray(self.get("lng")[::self.m]), self.get("mask")
+
     def window_lng(self, w):
         out = np.zeros(self.B)
         e = C.c_int(0)
@@ -307,3 +312,70 @@ class Server:
         check(self._L.rewl_server_info(self._h, _ptr(c), C.byref(f)))
         return {"queued": int(c[0]), "running": int(c[1]), "done": int(c[2]), "failed": int(c[3]),
                 "rounds": int(c[4]), "flips": int(c[5]), "pool_free": f.value}
+
+
+# ---- analysis of a joined ln g (host functions of the library) --------------
+def _lng_arg(lng):
+    return np.ascontiguousarray(lng, dtype=np.float64)
+
+
+def canonical(lng, T):
+    """Per-spin (u, c, f, s) at each temperature of T (Sec. 3.1, Fig. 3b)."""
+    v = _lng_arg(lng)
+    t = np.ascontiguousarray(np.atleast_1d(T), dtype=np.float64)
+    out = np.zeros((t.size, 4))
+    check(_lib.load().rewl_canonical(_ptr(v), v.size, _ptr(t), t.size, _ptr(out)))
+    return out[:, 0].copy(), out[:, 1].copy(), out[:, 2].copy(), out[:, 3].copy()
+
+
+def canonical_distribution(lng, T):
+    """P(E) at T scaled to 1 at its highest point (Fig. 3b)."""
+    v = _lng_arg(lng)
+    out = np.zeros(v.size)
+    check(_lib.load().rewl_canonical_distribution(_ptr(v), v.size, float(T), _ptr(out)))
+    return out
+
+
+def specific_heat_peak(lng, T_lo, T_hi):
+    """(T, c) at the largest specific heat for T in [T_lo, T_hi]."""
+    v = _lng_arg(lng)
+    T, c = C.c_double(), C.c_double()
+    check(_lib.load().rewl_specific_heat_peak(_ptr(v), v.size, float(T_lo), float(T_hi), C.byref(T), C.byref(c)))
+    return T.value, c.value
+
+
+def equal_peak_temperature(lng, T_lo, T_hi):
+    """(Tc, E_low, E_high, ln suppression): the two equal canonical peaks of a
+    first-order transition (Sec. 3.1)."""
+    v = _lng_arg(lng)
+    T, a, b, s = C.c_double(), C.c_int(), C.c_int(), C.c_double()
+    check(_lib.load().rewl_equal_peak_temperature(_ptr(v), v.size, float(T_lo), float(T_hi), C.byref(T), C.byref(a),
+                                                  C.byref(b), C.byref(s)))
+    return T.value, a.value, b.value, s.value
+
+
+def _pieces(e_lo, lng_w, mask_w):
+    e = np.ascontiguousarray(e_lo, dtype=np.int32)
+    return e, np.ascontiguousarray(lng_w, dtype=np.float64), np.ascontiguousarray(mask_w, dtype=np.uint8)
+
+
+def join(q, L, e_lo, W, lng_w, mask_w):
+    """Joined, normalised ln g from window pieces lng_w, mask_w of shape (h, W+1)."""
+    e, lw, mw = _pieces(e_lo, lng_w, mask_w)
+    out = np.zeros(2 * L * L + 1)
+    check(_lib.load().rewl_join(q, L, e.size, W, _ptr(e), _ptr(lw), _ptr(mw), _ptr(out), out.size))
+    return out
+
+
+def bootstrap(q, L, e_lo, W, lng_runs, mask_runs, draws):
+    """One joined, normalised ln g per row of draws: resample k averages the
+    window pieces of runs draws[k] (arrays of shape (runs, h, W+1))."""
+    e, lw, mw = _pieces(e_lo, lng_runs, mask_runs)
+    d = np.ascontiguousarray(np.atleast_2d(draws), dtype=np.int32)
+    runs = lw.shape[0]
+    if d.shape[1] != runs or lw.shape != (runs, e.size, W + 1) or mw.shape != lw.shape:
+        raise ValueError("pieces must be (runs, h, W+1) and every row of draws must name `runs` runs")
+    out = np.zeros((d.shape[0], 2 * L * L + 1))
+    check(_lib.load().rewl_bootstrap(q, L, e.size, W, _ptr(e), runs, _ptr(lw), _ptr(mw), d.shape[0], _ptr(d),
+                                     _ptr(out), out.shape[1]))
+    return out
