@@ -501,6 +501,28 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+def analyse(r, p):
+    """Canonical analysis of a converged run's joined ln g through the
+    library: the specific-heat maximum and the equal-peak temperature Tc(L)
+    with the suppression of the transition states (Sec. 3.1), searched within
+    [0.8, 1.3] x the exact infinite-lattice Tc = 1 / ln(1 + sqrt(q))."""
+    import math
+
+    import paper_1312_3004_gb300 as P
+
+    lng = r.lng()
+    tc_inf = 1.0 / math.log(1.0 + math.sqrt(p["q"]))
+    lo, hi = 0.8 * tc_inf, 1.3 * tc_inf
+    T, c = P.specific_heat_peak(lng, lo, hi)
+    out = {"T_range": [lo, hi], "c_peak_T": T, "c_peak": c, "Tc_equal_peak": None}
+    try:
+        Tc, a, b, sup = P.equal_peak_temperature(lng, lo, hi)
+        out.update({"Tc_equal_peak": Tc, "E_peaks": [a, b], "log10_suppression": sup / math.log(10.0)})
+    except P.RewlError:
+        pass  # no double peak in the range (a continuous transition)
+    return out
+
+
 def run_converge(args):
     """Time to convergence (every window at ln f < ln f_final) of full runs,
     one per seed: wall time of rewl_run from the created handle (set-up and
@@ -533,7 +555,8 @@ def run_converge(args):
             secs = finish.get(seed, el)
             runs.append({"seed": seed, "converged": seed in finish, "seconds": secs, "rounds": s["rounds"],
                          "flips": s["flips"], "mean_flips_per_s": s["flips"] / secs,
-                         "windows_done": s["windows_done"], "progress": []})
+                         "windows_done": s["windows_done"], "progress": [],
+                         "analysis": analyse(r, p) if seed in finish else None})
             r.close()
     for seed in ([] if args.concurrent else seeds):
         r = REWL(*WL.rewl_args(p, seed), spin_bits=p["spin_bits"])
@@ -552,7 +575,7 @@ def run_converge(args):
         s = r.stats()
         runs.append({"seed": seed, "converged": bool(conv), "seconds": el, "rounds": s["rounds"],
                      "flips": s["flips"], "mean_flips_per_s": s["flips"] / el, "windows_done": s["windows_done"],
-                     "progress": trace})
+                     "progress": trace, "analysis": analyse(r, p) if conv else None})
         print(json.dumps({"seed_done": runs[-1]}), flush=True)
         r.close()
     done = [x["seconds"] for x in runs if x["converged"]]
