@@ -57,7 +57,7 @@ def lib():
         L.orc_dims.restype = None
         for name in ("orc_get_e_lo", "orc_get_sigma", "orc_get_E", "orc_get_rep", "orc_get_t",
                      "orc_get_lng", "orc_get_H", "orc_get_mask", "orc_get_lnf", "orc_get_iter",
-                     "orc_get_done", "orc_get_xstats", "orc_get_rt_end", "orc_get_rt_trips",
+                     "orc_get_done", "orc_get_xstats", "orc_get_rt_end", "orc_get_rt_trips", "orc_get_phase",
                      "orc_set_lng", "orc_set_lnf", "orc_set_H",
                      "orc_set_mask"):
             getattr(L, name).argtypes = [vp, vp]
@@ -66,6 +66,10 @@ def lib():
         L.orc_set_config.restype = None
         L.orc_set_round.argtypes = [vp, i64]
         L.orc_set_round.restype = None
+        L.orc_set_schedule.argtypes = [vp, i32]
+        L.orc_set_schedule.restype = None
+        L.orc_walker_visited_all.argtypes = [vp, i32]
+        L.orc_walker_visited_all.restype = i32
         L.ex_brute_force.argtypes = [i32, i32, vp]
         L.ex_brute_force.restype = i32
         L.ex_transfer_matrix.argtypes = [i32, i32, i32, vp, vp]
@@ -195,6 +199,14 @@ class OracleREWL:
     def xstats(self): return self._get("orc_get_xstats", 2, np.uint64)
     def rt_end(self): return self._get("orc_get_rt_end", self.G, np.uint8)
     def rt_trips(self): return self._get("orc_get_rt_trips", self.G, np.uint32)
+    def phase(self): return self._get("orc_get_phase", self.h, np.uint8)
+
+    def set_schedule(self, schedule):
+        """0: ln f halves per iteration (Sec. 2); 1: the 1/t rule."""
+        lib().orc_set_schedule(self._h, schedule)
+
+    def walker_visited_all(self, g):
+        return bool(lib().orc_walker_visited_all(self._h, g))
 
     def set_lng(self, v):
         a = np.ascontiguousarray(np.broadcast_to(v, (self.G, self.B)), dtype=np.float64)

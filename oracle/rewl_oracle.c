@@ -188,6 +188,8 @@ typedef struct orc_rewl {
                         2 highest window)                                      */
     uint32_t *rt_trips; /* [h*m] by replica id: completed round trips, lowest
                         window -> highest -> lowest                            */
+    int schedule;    /* ln f schedule: 0 halving (Sec. 2), 1 the 1/t rule     */
+    uint8_t *phase;  /* [h] 1/t rule: 1 once the window follows ln f = 1/t   */
     int64_t round;   /* barriers (exchange rounds) completed                  */
     uint64_t xtried, xacc;
     int status;
@@ -200,7 +202,7 @@ void orc_destroy(orc_rewl *s)
     if (!s) return;
     free(s->e_lo); free(s->sigma); free(s->E); free(s->rep); free(s->t);
     free(s->lng); free(s->H); free(s->mask); free(s->lnf); free(s->iter); free(s->done);
-    free(s->rt_end); free(s->rt_trips);
+    free(s->rt_end); free(s->rt_trips); free(s->phase);
     free(s);
 }
 
@@ -295,8 +297,9 @@ orc_rewl *orc_create(int q, int L, int h, double overlap, int m, double lnf_fina
     s->done = calloc((size_t)h, 1);
     s->rt_end = calloc(G, 1);
     s->rt_trips = calloc(G, sizeof(uint32_t));
+    s->phase = calloc((size_t)h, 1);
     if (!s->e_lo || !s->sigma || !s->E || !s->rep || !s->t || !s->lng || !s->H || !s->mask ||
-        !s->lnf || !s->iter || !s->done || !s->rt_end || !s->rt_trips) {
+        !s->lnf || !s->iter || !s->done || !s->rt_end || !s->rt_trips || !s->phase) {
         orc_destroy(s);
         return NULL;
     }
@@ -411,9 +414,36 @@ int orc_walker_flat(const orc_rewl *s, int g)
     return (double)mn >= s->flatness * ((double)sum / (double)n);
 }
 
+/* Criterion of the first stage of the 1/t rule (Belardinelli & Pereyra,
+ * Phys. Rev. E 75, 046701 (2007)): walker g has visited every bin of its
+ * window's mask at least once since H was last cleared. */
+int orc_walker_visited_all(const orc_rewl *s, int g)
+{
+    size_t B = (size_t)s->W + 1;
+    int w = g / s->m;
+    const uint32_t *Hg = s->H + (size_t)g * B;
+    const uint8_t *mk = s->mask + (size_t)w * B;
+    int n = 0;
+    for (size_t b = 0; b < B; ++b) {
+        if (!mk[b]) continue;
+        n += 1;
+        if (Hg[b] == 0) return 0;
+    }
+    return n > 0;
+}
+
 /* (c) A window whose m walkers are all flat averages and redistributes ln g,
  * clears H and moves to ln f / 2 (f -> sqrt f); it is finished once
- * ln f < ln f_final (Sec. 2). */
+ * ln f < ln f_final (Sec. 2).
+ *
+ * With the 1/t rule (schedule 1; Sec. 2 notes that the scheme works with any
+ * valid WL update rule; the rule is Belardinelli & Pereyra's): the iteration
+ * criterion is "every mask bin visited" instead of flatness; at the end of an
+ * iteration ln f is halved unless the half falls below 1/t, where
+ * t = (WL steps per walker) / (bins in the window's mask), and from then on the
+ * window follows ln f = 1/t: at every barrier its walkers' ln g are merged,
+ * H is cleared and ln f = 1/t is taken with the current t (held over the next
+ * K steps).  Finished once ln f < ln f_final, as with halving. */
 void orc_window_iterations(orc_rewl *s)
 {
     size_t B = (size_t)s->W + 1;
@@ -421,21 +451,47 @@ void orc_window_iterations(orc_rewl *s)
     double *col = (double *)malloc(sizeof(double) * (size_t)m);
     for (int w = 0; w < s->h; ++w) {
         if (s->done[w]) continue;
-        int all_flat = 1;
-        for (int k = 0; k < m; ++k) all_flat &= orc_walker_flat(s, w * m + k);
-        if (!all_flat) continue;
+        int inv_t = s->schedule == 1;
+        int follows_1t = inv_t && s->phase[w];
+        if (!follows_1t) {
+            int all_flat = 1;
+            for (int k = 0; k < m; ++k)
+                all_flat &= inv_t ? orc_walker_visited_all(s, w * m + k) : orc_walker_flat(s, w * m + k);
+            if (!all_flat) continue;
+        }
         for (size_t b = 0; b < B; ++b) {
             for (int k = 0; k < m; ++k) col[k] = s->lng[((size_t)w * m + k) * B + b];
             double mean = orc_tree_mean(col, m);
             for (int k = 0; k < m; ++k) s->lng[((size_t)w * m + k) * B + b] = mean;
         }
         for (int k = 0; k < m; ++k) memset(s->H + ((size_t)w * m + k) * B, 0, B * sizeof(uint32_t));
-        s->lnf[w] = s->lnf[w] * 0.5;
-        s->iter[w] += 1;
+        if (!inv_t) {
+            s->lnf[w] = s->lnf[w] * 0.5;
+            s->iter[w] += 1;
+        } else {
+            int n_bins = 0;
+            for (size_t b = 0; b < B; ++b) n_bins += s->mask[(size_t)w * B + b] != 0;
+            uint64_t steps = s->t[(size_t)w * m];
+            double one_over_t = steps ? (double)n_bins / (double)steps : 0.0;
+            if (follows_1t) {
+                s->lnf[w] = one_over_t;
+            } else {
+                double half = s->lnf[w] * 0.5;
+                s->iter[w] += 1;
+                if (half < one_over_t) {
+                    s->phase[w] = 1;
+                    s->lnf[w] = one_over_t;
+                } else {
+                    s->lnf[w] = half;
+                }
+            }
+        }
         if (s->lnf[w] < s->lnf_final) s->done[w] = 1;
     }
     free(col);
 }
+
+void orc_set_schedule(orc_rewl *s, int schedule) { s->schedule = schedule; }
 
 /* (d) Replica exchange between windows a and a+1 for every a with
  * a = round (mod 2) where neither window has finished.  Walker k of window a
@@ -644,6 +700,7 @@ void orc_get_iter(const orc_rewl *s, int32_t *o) { memcpy(o, s->iter, sizeof(int
 void orc_get_done(const orc_rewl *s, uint8_t *o) { memcpy(o, s->done, (size_t)s->h); }
 void orc_get_xstats(const orc_rewl *s, uint64_t o[2]) { o[0] = s->xtried; o[1] = s->xacc; }
 void orc_get_rt_end(const orc_rewl *s, uint8_t *o) { memcpy(o, s->rt_end, (size_t)s->h * s->m); }
+void orc_get_phase(const orc_rewl *s, uint8_t *o) { memcpy(o, s->phase, (size_t)s->h); }
 void orc_get_rt_trips(const orc_rewl *s, uint32_t *o)
 {
     memcpy(o, s->rt_trips, sizeof(uint32_t) * (size_t)s->h * s->m);
