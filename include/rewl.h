@@ -143,8 +143,9 @@ rewl_status rewl_run_async(rewl_t h, long long rounds);
 enum { REWL_PHASE_SWEEP = 0, REWL_PHASE_CHECK = 1, REWL_PHASE_EXCHANGE = 2 };
 rewl_status rewl_run_phase(rewl_t h, int phase);
 
-/* Tuning options of a handle (no counterpart in the paper, and no effect on
- * results: every choice computes the same states bit for bit):
+/* Options of a handle.  All but REWL_OPT_SCHEDULE are tuning options (no
+ * counterpart in the paper, and no effect on results: every choice computes
+ * the same states bit for bit):
  *   REWL_OPT_SWEEP_KERNEL  0 = fast sweep (integer acceptance path with a
  *                          binary64 fallback), 1 = binary64 reference sweep
  *   REWL_OPT_LANES         lanes per walker of the fast sweep: 0 = chosen from
@@ -160,17 +161,31 @@ rewl_status rewl_run_phase(rewl_t h, int phase);
  *                          get: 1 if the current plan keeps them in global
  *                          memory, else 0
  *   REWL_OPT_STALL_MS      stall watchdog of rewl_run: when no window has
- *                          finished an iteration for this many milliseconds
+ *                          finished an iteration (or follows ln f = 1/t, which
+ *                          falls every round) for this many milliseconds
  *                          of the call, rewl_run stops at a round boundary
  *                          and returns REWL_ERR_TIMEOUT (the state stays valid
  *                          and the run can go on); 0 (default) = off
+ *   REWL_OPT_SCHEDULE      the ln f schedule of every window (Sec. 2 states that
+ *                          the scheme works with any valid WL update rule):
+ *                          0 (default) = ln f / 2 once all m walkers are flat
+ *                          (Sec. 2); 1 = the 1/t rule of Belardinelli & Pereyra
+ *                          (Phys. Rev. E 75, 046701): an iteration ends once every
+ *                          walker has visited every bin of the window's mask
+ *                          (flatness is not used), ln f is halved unless the
+ *                          half is below 1/t with t = WL steps per walker / bins
+ *                          in the mask, and from then on (REWL_FIELD_PHASE = 1)
+ *                          every barrier merges the window's walkers, clears H
+ *                          and sets ln f = 1/t; done once ln f < lnf_final.  Set
+ *                          it at a round boundary; rounds run before keep their
+ *                          schedule.  Not available on batch instances.
  * rewl_set_option synchronises the stream and re-plans the sweep (not for
  * REWL_OPT_STALL_MS).
  * Errors: REWL_ERR_ARG (unknown option or value, or a plan that does not fit
  * in shared memory). */
 enum {
     REWL_OPT_SWEEP_KERNEL = 0, REWL_OPT_LANES = 1, REWL_OPT_WALKERS_PER_CTA = 2, REWL_OPT_LATTICE = 3,
-    REWL_OPT_STALL_MS = 4
+    REWL_OPT_STALL_MS = 4, REWL_OPT_SCHEDULE = 5
 };
 rewl_status rewl_set_option(rewl_t h, int option, long long value);
 rewl_status rewl_get_option(rewl_t h, int option, long long *value);
@@ -228,12 +243,14 @@ rewl_status rewl_get_stats(rewl_t h, rewl_stats *stats);
  *   REWL_FIELD_TRIP_END uint8 [h*m]    by replica id c: last end of the range its
  *                                      window touched: 0 none yet, 1 window 0,
  *                                      2 window h-1
+ *   REWL_FIELD_PHASE  uint8  [h]       1/t rule (REWL_OPT_SCHEDULE = 1): 1 once window i
+ *                                      follows ln f = 1/t, else 0
  * bytes must equal the size above, else REWL_ERR_ARG. */
 enum {
     REWL_FIELD_SPINS = 0, REWL_FIELD_ENERGY = 1, REWL_FIELD_REPLICA = 2, REWL_FIELD_STEPS = 3,
     REWL_FIELD_LNG = 4, REWL_FIELD_HIST = 5, REWL_FIELD_MASK = 6, REWL_FIELD_LNF = 7,
     REWL_FIELD_ITER = 8, REWL_FIELD_DONE = 9, REWL_FIELD_ELO = 10, REWL_FIELD_ROUND = 11,
-    REWL_FIELD_TRIPS = 12, REWL_FIELD_TRIP_END = 13
+    REWL_FIELD_TRIPS = 12, REWL_FIELD_TRIP_END = 13, REWL_FIELD_PHASE = 14
 };
 rewl_status rewl_get_field(rewl_t h, int field, void *out, size_t bytes);
 
@@ -246,9 +263,10 @@ rewl_status rewl_set_field(rewl_t h, int field, const void *in, size_t bytes);
 /* Checkpoint and resume (no counterpart in the paper).
  * Serialise the whole state (at a round boundary) into `buf` (host).  With
  * buf == NULL only *len is set to the required size.  rewl_load restores it
- * into a handle created with the same parameters; run(2K) equals
- * run(K) + save + load + run(K) bit for bit.  Errors: REWL_ERR_ARG (buffer too
- * small, or a blob of other parameters / corrupted). */
+ * into a handle created with the same parameters and set to the same ln f
+ * schedule; run(2K) equals run(K) + save + load + run(K) bit for bit.
+ * Errors: REWL_ERR_ARG (buffer too small, or a blob of other parameters or
+ * schedule / corrupted). */
 rewl_status rewl_save(rewl_t h, void *buf, size_t *len);
 rewl_status rewl_load(rewl_t h, const void *buf, size_t len);
 

@@ -235,6 +235,8 @@ struct SaveHeader {
     char magic[8];
     uint32_t version;
     uint32_t spin_bits;
+    uint32_t schedule;
+    uint32_t pad;
     rewl_params prm;
     uint64_t payload;
     uint64_t checksum;
@@ -310,6 +312,7 @@ rewl_status prepare_instance(rewl_s *h, const rewl_params &p, int spin_bits, int
     M.K = p.exchange_interval;
     M.lnf_final = p.lnf_final;
     M.flatness = p.flatness;
+    M.schedule = rewl::SCHED_HALVING;
     cudaError_t e = cudaGetDevice(&h->device);
     if (e != cudaSuccess) return fail(REWL_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
     cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
@@ -320,7 +323,7 @@ rewl_status prepare_instance(rewl_s *h, const rewl_params &p, int spin_bits, int
                     rewl::fast_smem_per_walker(M, h->plan.lanes, h->plan.lat_global != 0), h->smem_optin);
     const size_t G = (size_t)M.G, B = (size_t)M.B, hh = (size_t)M.h;
     const size_t sizes[] = {G * M.wpc * 4, G * 4, G * 4, G * 8, G * B * 8, G * B * 4, hh * B, hh * 4, hh * 8, hh * 4, hh,
-                            G, G * 4, G * (B + 2 * rewl::kShadowPad) * 8, sizeof(Ctl)};
+                            G, G * 4, G * (B + 2 * rewl::kShadowPad) * 8, hh, sizeof(Ctl)};
     size_t off = 0;
     h->parts.clear();
     for (size_t sz : sizes) {
@@ -349,7 +352,8 @@ void carve_instance(rewl_s *h, void *base) {
     S.rt_end = (uint8_t *)at(11);
     S.rt_trips = (uint32_t *)at(12);
     S.shadow = (long long *)at(13);
-    S.ctl = (Ctl *)at(14);
+    S.phase = (uint8_t *)at(14);
+    S.ctl = (Ctl *)at(15);  // last: save / load treat the last part as the control block
 }
 
 cudaError_t init_instance_async(rewl_s *h, cudaStream_t s) {
@@ -474,7 +478,12 @@ rewl_status rewl_set_option(rewl_t h, int option, long long value) {
         h->stall_ms = value;
         return REWL_OK;
     }
-    if (option == REWL_OPT_SWEEP_KERNEL) {
+    int schedule = h->M.schedule;
+    if (option == REWL_OPT_SCHEDULE) {
+        if (value != rewl::SCHED_HALVING && value != rewl::SCHED_INV_T)
+            return fail(REWL_ERR_ARG, "ln f schedule %lld not 0 or 1", value);
+        schedule = (int)value;
+    } else if (option == REWL_OPT_SWEEP_KERNEL) {
         if (value != 0 && value != 1) return fail(REWL_ERR_ARG, "sweep kernel %lld not 0 or 1", value);
         kind = value == 0 ? rewl::SWEEP_FAST : rewl::SWEEP_REFERENCE;
         lanes = 0;
@@ -494,6 +503,7 @@ rewl_status rewl_set_option(rewl_t h, int option, long long value) {
     REWL_CUDA(rewl::prepare_sweep(h->M, plan));
     h->plan = plan;
     h->lat_mode = lat_mode;
+    h->M.schedule = schedule;
     if (h->graph) {
         cudaGraphExecDestroy(h->graph);
         h->graph = nullptr;
@@ -508,6 +518,7 @@ rewl_status rewl_get_option(rewl_t h, int option, long long *value) {
     else if (option == REWL_OPT_WALKERS_PER_CTA) *value = h->plan.P;
     else if (option == REWL_OPT_LATTICE) *value = h->plan.lat_global;
     else if (option == REWL_OPT_STALL_MS) *value = h->stall_ms;
+    else if (option == REWL_OPT_SCHEDULE) *value = h->M.schedule;
     else return fail(REWL_ERR_ARG, "unknown option %d", option);
     return REWL_OK;
 }
@@ -525,8 +536,10 @@ rewl_status rewl_run(rewl_t h, long long max_rounds, int *converged) {
     if (!h) return fail(REWL_ERR_ARG, "NULL handle");
     long long left = max_rounds;
     rewl_status st = read_ctl(h);
-    // stall watchdog: progress = iterations completed over all windows
+    // stall watchdog: progress = iterations completed over all windows; a
+    // window that follows ln f = 1/t lowers ln f every round, so it progresses
     std::vector<int32_t> iters(h->stall_ms > 0 ? (size_t)h->M.h : 0);
+    std::vector<uint8_t> phase(h->stall_ms > 0 ? (size_t)h->M.h : 0), done(phase.size());
     long long progress = -1;
     auto t_progress = std::chrono::steady_clock::now();
     while (st == REWL_OK && !h->h_ctl->all_done && (max_rounds <= 0 || left > 0)) {
@@ -538,8 +551,14 @@ rewl_status rewl_run(rewl_t h, long long max_rounds, int *converged) {
             REWL_CUDA(cudaMemcpy(iters.data(), h->S.iter, iters.size() * 4, cudaMemcpyDeviceToHost));
             long long sum = 0;
             for (int32_t v : iters) sum += v;
+            bool moving = false;
+            if (h->M.schedule == rewl::SCHED_INV_T) {
+                REWL_CUDA(cudaMemcpy(phase.data(), h->S.phase, phase.size(), cudaMemcpyDeviceToHost));
+                REWL_CUDA(cudaMemcpy(done.data(), h->S.done, done.size(), cudaMemcpyDeviceToHost));
+                for (size_t w = 0; w < phase.size(); ++w) moving = moving || (phase[w] && !done[w]);
+            }
             const auto now = std::chrono::steady_clock::now();
-            if (sum != progress) {
+            if (sum != progress || moving) {
                 progress = sum;
                 t_progress = now;
             } else if (std::chrono::duration_cast<std::chrono::milliseconds>(now - t_progress).count() > h->stall_ms) {
@@ -637,6 +656,7 @@ static rewl_status field_geometry(rewl_t h, int field, void **dev, size_t *bytes
     case REWL_FIELD_ROUND: *dev = &h->S.ctl->round; *bytes = 8; break;
     case REWL_FIELD_TRIPS: *dev = h->S.rt_trips; *bytes = G * 4; break;
     case REWL_FIELD_TRIP_END: *dev = h->S.rt_end; *bytes = G; break;
+    case REWL_FIELD_PHASE: *dev = h->S.phase; *bytes = hh; break;
     default: return fail(REWL_ERR_ARG, "unknown field %d", field);
     }
     return REWL_OK;
@@ -719,8 +739,9 @@ rewl_status rewl_save(rewl_t h, void *buf, size_t *len) {
     SaveHeader hd;
     std::memset(&hd, 0, sizeof hd);
     std::memcpy(hd.magic, "REWLSAV1", 8);
-    hd.version = 1;
+    hd.version = 2;
     hd.spin_bits = (uint32_t)h->M.bits;
+    hd.schedule = (uint32_t)h->M.schedule;
     hd.prm = h->prm;
     hd.payload = payload;
     hd.checksum = fnv1a((const unsigned char *)buf + sizeof(SaveHeader), payload);
@@ -736,10 +757,13 @@ rewl_status rewl_load(rewl_t h, const void *buf, size_t len) {
     std::memcpy(&hd, buf, sizeof hd);
     size_t payload = 0;
     for (auto &p : h->parts) payload += p.bytes;
-    if (std::memcmp(hd.magic, "REWLSAV1", 8) != 0 || hd.version != 1) return fail(REWL_ERR_ARG, "not a rewl state blob");
+    if (std::memcmp(hd.magic, "REWLSAV1", 8) != 0 || hd.version != 2) return fail(REWL_ERR_ARG, "not a rewl state blob");
     if (hd.payload != payload || len != sizeof(SaveHeader) + payload || hd.spin_bits != (uint32_t)h->M.bits ||
         !same_params(hd.prm, h->prm))
         return fail(REWL_ERR_ARG, "blob belongs to an instance with other parameters");
+    if (hd.schedule != (uint32_t)h->M.schedule)
+        return fail(REWL_ERR_ARG, "blob was saved under ln f schedule %u, the handle runs %d", hd.schedule,
+                    h->M.schedule);
     if (fnv1a((const unsigned char *)buf + sizeof(SaveHeader), payload) != hd.checksum)
         return fail(REWL_ERR_ARG, "blob checksum mismatch (corrupted)");
     const unsigned char *src = (const unsigned char *)buf + sizeof(SaveHeader);

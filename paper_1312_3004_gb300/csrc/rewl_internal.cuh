@@ -43,7 +43,13 @@ struct Model {
     uint32_t divL;            // ceil(2^32 / L) for site -> (x, y)
     long long K;              // WL steps per walker between exchanges
     double lnf_final, flatness;
+    int schedule;             // ln f schedule: SCHED_HALVING or SCHED_INV_T
 };
+
+// ln f schedules of the window check: halving per iteration (Sec. 2), or the
+// 1/t rule (Belardinelli & Pereyra), which Sec. 2 admits as another valid WL
+// update rule.
+enum : int { SCHED_HALVING = 0, SCHED_INV_T = 1 };
 
 struct State {
     uint32_t *spins;      // [G][wpc] packed configurations, by buffer id
@@ -61,6 +67,7 @@ struct State {
     uint32_t *rt_trips;   // [G] by replica id: completed round trips (lowest window -> highest -> lowest)
     long long *shadow;    // [G][B + 2 kShadowPad] ln g shadows of the one-lane sweep that keeps
                           // every walker's state in global memory
+    uint8_t *phase;       // [h] 1/t rule: 1 once the window follows ln f = 1/t
     Ctl *ctl;             // control block
 };
 

@@ -248,6 +248,11 @@ __global__ void __launch_bounds__(256) sweep_kernel(Model M, State S, int P) {
 // the m walkers' values (pairwise tree in walker order: stride 1, 2, 4, ...,
 // an element without partner passes through; then / m), H <- 0,
 // ln f <- ln f / 2 (f -> sqrt f); the window is finished once ln f < ln f_final.
+// Under the 1/t rule (SCHED_INV_T, Belardinelli & Pereyra) the criterion of (b)
+// is "every mask bin visited" (min H >= 1); at the end of an iteration ln f is
+// halved unless the half falls below 1/t, t = WL steps per walker / bins in
+// the mask, after which the window follows ln f = 1/t: merge and H <- 0 at
+// every barrier, ln f = 1/t with the current t.
 constexpr int MAX_M = 256;  // walkers per window (exchange permutation buffer)
 constexpr int CHECK_THREADS = 256;
 
@@ -273,9 +278,12 @@ __device__ void window_check_block(const Model &M, const State &S, int w) {
         return;
     }
 
+    const bool inv_t = M.schedule == SCHED_INV_T;
+    const bool follows_1t = inv_t && S.phase[w];
     __shared__ unsigned int r_n[CHECK_THREADS / 32], r_mn[CHECK_THREADS / 32];
     __shared__ unsigned long long r_sum[CHECK_THREADS / 32];
     __shared__ int all_flat;
+    __shared__ unsigned int n_bins;  // bins in the window's mask
     if (tid == 0) all_flat = 1;
     for (int k = 0; k < m; ++k) {
         unsigned int n = 0, mn = 0xffffffffu;
@@ -308,12 +316,13 @@ __device__ void window_check_block(const Model &M, const State &S, int w) {
                 ts += r_sum[i];
                 tmn = min(tmn, r_mn[i]);
             }
-            const bool flat = tn > 0 && (double)tmn >= M.flatness * ((double)ts / (double)tn);
+            const bool flat = tn > 0 && (inv_t ? tmn >= 1u : (double)tmn >= M.flatness * ((double)ts / (double)tn));
             if (!flat) all_flat = 0;
+            n_bins = tn;
         }
     }
     __syncthreads();
-    if (!all_flat) return;
+    if (!all_flat && !follows_1t) return;
 
     // Merge: the pairwise tree is formed in place in the walkers' own rows (they
     // are overwritten by the mean afterwards); each thread owns whole bins.
@@ -329,9 +338,25 @@ __device__ void window_check_block(const Model &M, const State &S, int w) {
         }
     }
     if (tid == 0) {
-        const double nl = S.lnf[w] * 0.5;
+        double nl;
+        if (!inv_t) {
+            nl = S.lnf[w] * 0.5;
+            S.iter[w] += 1;
+        } else {
+            const unsigned long long steps = S.t[(size_t)w * m];
+            const double one_over_t = steps ? __ddiv_rn((double)n_bins, (double)steps) : 0.0;
+            if (follows_1t) {
+                nl = one_over_t;
+            } else {
+                nl = S.lnf[w] * 0.5;
+                S.iter[w] += 1;
+                if (nl < one_over_t) {
+                    S.phase[w] = 1;
+                    nl = one_over_t;
+                }
+            }
+        }
         S.lnf[w] = nl;
-        S.iter[w] += 1;
         if (nl < M.lnf_final) S.done[w] = 1;
     }
 }

@@ -112,11 +112,11 @@ extern "C" rewl_status rewl_run_static(const rewl_params *prm, int spin_bits, lo
     const size_t G = (size_t)M.G, B = (size_t)M.B, hh = (size_t)M.h;
     if (out_bins != hh * B) return fail_static(REWL_ERR_ARG, "out_bins %zu != h * (W + 1) = %zu", out_bins, hh * B);
 
-    const size_t sizes[15] = {G * M.wpc * 4, G * 4, G * 4, G * 8, G * B * 8, G * B * 4,
+    const size_t sizes[16] = {G * M.wpc * 4, G * 4, G * 4, G * 8, G * B * 8, G * B * 4,
                               hh * B, hh * 4, hh * 8, hh * 4, hh, G, G * 4, G * (B + 2 * rewl::kShadowPad) * 8,
-                              sizeof(rewl::Ctl)};
-    size_t offs[15], total = 0;
-    for (int i = 0; i < 15; ++i) {
+                              hh, sizeof(rewl::Ctl)};
+    size_t offs[16], total = 0;
+    for (int i = 0; i < 16; ++i) {
         offs[i] = total;
         total += round256(sizes[i]);
     }
@@ -147,7 +147,8 @@ extern "C" rewl_status rewl_run_static(const rewl_params *prm, int spin_bits, lo
     S.rt_end = (uint8_t *)(base + offs[11]);
     S.rt_trips = (uint32_t *)(base + offs[12]);
     S.shadow = (long long *)(base + offs[13]);
-    S.ctl = (rewl::Ctl *)(base + offs[14]);
+    S.phase = (uint8_t *)(base + offs[14]);
+    S.ctl = (rewl::Ctl *)(base + offs[15]);
 
     cudaStream_t s = (cudaStream_t)stream;
     const rewl::SweepPlan plan = rewl::plan_sweep(M, sms, (size_t)optin);
