@@ -59,6 +59,9 @@ def parse_args():
                          "batched2048 or serving")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--schedule", default="halving", choices=["halving", "inv_t"],
+                    help="inv_t: every window starts in the 1/t stage (ln f = bins / steps, not a power of "
+                         "two, so every WL step takes the binary64 add)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--jobs", type=int, default=100, help="arrivals of the serving trace")
     ap.add_argument("--converge", default="",
@@ -265,6 +268,9 @@ def run_ours(args):
     p = WL.params(args.workload)
     stream = torch.cuda.Stream()
     r = REWL(*WL.rewl_args(p, args.seed + rank), spin_bits=p["spin_bits"], stream=stream)
+    if args.schedule == "inv_t":
+        r.set_option(_lib.OPT_SCHEDULE, _lib.SCHEDULE_INV_T)
+        r.set("phase", 1)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def one_step(ev):
@@ -337,10 +343,14 @@ def run_ours(args):
         "metric": "flip attempts/s", "value": value, "unit": "flips/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": dict(config_of(args.workload, p), parallelism="replicas" if world > 1 else "single"),
+        "data": "synthetic", "config": dict(config_of(args.workload, p), parallelism="replicas" if world > 1 else "single",
+                                            lnf_schedule=args.schedule),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                     "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH.get(args.workload),
-                     "kernel": "sweep_kernel", "avg_launch_ms": sweep_avg_s * 1e3,
+                     "frac": achieved / peak,
+                     # the ncu figures were taken on the halving schedule's fast sweep
+                     "traffic": TRAFFIC_PER_LAUNCH.get(args.workload) if args.schedule == "halving" else None,
+                     "kernel": "sweep_fast_kernel" if r.get_option(_lib.OPT_SWEEP_KERNEL) == 0 else "sweep_kernel",
+                     "avg_launch_ms": sweep_avg_s * 1e3,
                      "ops_per_flip": ALG_OPS_PER_FLIP,
                      "peak_basis": "152 SMs x 128 INT32/FP32 lanes x 2070 MHz (recipe unit counts)",
                      # each walker's steps form one dependent chain: the clock cycles
