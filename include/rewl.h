@@ -470,6 +470,14 @@ rewl_status rewl_bootstrap(int q, int L, int h, int W, const int *e_lo, int runs
  * misaligned pointer) makes the creating call fail with REWL_ERR_NOMEM. */
 void rewl_set_allocator(void *(*alloc)(size_t bytes, void *ctx), void (*free)(void *ptr, void *ctx), void *ctx);
 
+/* Ising energy of the bin b = E + 2N of a q = 2 run (b broken bonds), in the
+ * Ising convention E_I = -sum over bonds of s_i s_j (J = 1): each broken bond
+ * counts +1 and each satisfied bond -1, so E_I = 2b - 2N = 2E + 2N with the
+ * Potts energy E of Eq. 2 (for L = 8: E_I in [-128, 128], in steps of 4 where
+ * g > 0).  *e_ising receives it.  Errors: REWL_ERR_ARG (L outside [3, 1024],
+ * b outside [0, 2N], NULL output). */
+rewl_status rewl_ising_energy(int L, int b, long long *e_ising);
+
 /* Message of the last error on this thread ("" if none).  No counterpart in
  * the paper. */
 const char *rewl_last_error(void);

@@ -127,8 +127,9 @@ def load():
     L.rewl_equal_peak_temperature.argtypes = [vp, sz, C.c_double, C.c_double, pd, pi, pi, pd]
     L.rewl_join.argtypes = [i32, i32, i32, i32, vp, vp, vp, vp, sz]
     L.rewl_bootstrap.argtypes = [i32, i32, i32, i32, vp, i32, vp, vp, i32, vp, vp, sz]
+    L.rewl_ising_energy.argtypes = [i32, i32, C.POINTER(C.c_longlong)]
     for name in ("rewl_canonical", "rewl_canonical_distribution", "rewl_specific_heat_peak",
-                 "rewl_equal_peak_temperature", "rewl_join", "rewl_bootstrap"):
+                 "rewl_equal_peak_temperature", "rewl_join", "rewl_bootstrap", "rewl_ising_energy"):
         getattr(L, name).restype = st
     L.rewl_last_error.argtypes = []
     L.rewl_last_error.restype = C.c_char_p

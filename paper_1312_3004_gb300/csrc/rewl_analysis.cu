@@ -213,6 +213,15 @@ rewl_status rewl_equal_peak_temperature(const double *lng, size_t len, double T_
     return REWL_OK;
 }
 
+rewl_status rewl_ising_energy(int L, int b, long long *e_ising) {
+    if (!e_ising) return fail(REWL_ERR_ARG, "NULL output");
+    if (L < 3 || L > 1024) return fail(REWL_ERR_ARG, "L=%d outside [3, 1024]", L);
+    const long long N = (long long)L * L;
+    if (b < 0 || b > 2 * N) return fail(REWL_ERR_ARG, "bin %d outside [0, 2N]", b);
+    *e_ising = 2LL * b - 2LL * N;
+    return REWL_OK;
+}
+
 }  // extern "C"
 
 namespace {

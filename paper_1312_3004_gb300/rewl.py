@@ -379,3 +379,10 @@ def bootstrap(q, L, e_lo, W, lng_runs, mask_runs, draws):
     check(_lib.load().rewl_bootstrap(q, L, e.size, W, _ptr(e), runs, _ptr(lw), _ptr(mw), d.shape[0], _ptr(d),
                                      _ptr(out), out.shape[1]))
     return out
+
+
+def ising_energy(L, b):
+    """Ising energy 2b - 2N of the bin with b broken bonds (q = 2)."""
+    e = C.c_longlong()
+    check(_lib.load().rewl_ising_energy(int(L), int(b), C.byref(e)))
+    return e.value

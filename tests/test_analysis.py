@@ -177,3 +177,21 @@ def test_analysis_arguments_are_checked():
     with pytest.raises(P.RewlError):
         P.bootstrap(2, 4, e_lo, W, lw[None], mw[None], [[1]])  # draw outside [0, runs)
     assert P.canonical(good, []) [0].size == 0
+
+
+def test_ising_energy_equals_the_spin_sum_on_every_configuration():
+    """rewl_ising_energy(L, b) against E_I = -sum over bonds of s_i s_j with
+    s = +-1, summed directly over every configuration of the 3x3 and 4x4 tori."""
+    _lib_or_skip()
+    for L in (3, 4):
+        N = L * L
+        codes = np.arange(2 ** N, dtype=np.int64)
+        s = ((codes[:, None] >> np.arange(N)) & 1).reshape(-1, L, L).astype(np.int64) * 2 - 1
+        e_ising = -(s * np.roll(s, 1, axis=1)).sum(axis=(1, 2)) - (s * np.roll(s, 1, axis=2)).sum(axis=(1, 2))
+        broken = (s != np.roll(s, 1, axis=1)).sum(axis=(1, 2)) + (s != np.roll(s, 1, axis=2)).sum(axis=(1, 2))
+        table = {b: P.ising_energy(L, b) for b in range(2 * N + 1)}
+        assert all(table[int(b)] == int(e) for b, e in zip(broken, e_ising))
+    assert (P.ising_energy(8, 0), P.ising_energy(8, 128), P.ising_energy(8, 4)) == (-128, 128, -120)
+    for bad in ((8, -1), (8, 129), (2, 0)):
+        with pytest.raises(P.RewlError):
+            P.ising_energy(*bad)
