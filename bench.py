@@ -533,6 +533,31 @@ def analyse(r, p):
     return out
 
 
+def oracle_reference(workload, seed, analysis):
+    """The oracle's converged values for this workload and seed, when stored
+    (tests/golden/<workload>_converged.json, written by a script that runs
+    only the oracle), with the oracle's mean and standard deviation over its
+    seeds: the GPU run of the same seed reproduces the oracle's run, so its
+    analysis must agree with the stored one."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden", workload + "_converged.json")
+    if analysis is None or not os.path.exists(path):
+        return None
+    with open(path) as f:
+        ref = json.load(f)
+    mine = [r for r in ref["runs"] if r["seed"] == seed]
+    out = {"oracle_seeds": len(ref["runs"]), "oracle_mean": ref["mean"], "oracle_sd": ref["sd"]}
+    if mine:
+        r = mine[0]
+        out["oracle_same_seed"] = {k: r[k] for k in ("c_peak_T", "c_peak", "Tc_equal_peak", "E_peaks")}
+        out["same_as_oracle"] = (abs(analysis["c_peak_T"] - r["c_peak_T"]) <= 1e-6 * r["c_peak_T"] and
+                                 abs(analysis["c_peak"] - r["c_peak"]) <= 1e-9 * r["c_peak"] and
+                                 analysis.get("E_peaks") == r["E_peaks"])
+    for key in ("c_peak_T", "c_peak", "Tc_equal_peak"):
+        if analysis.get(key) is not None and ref["sd"][key] > 0:
+            out.setdefault("sigmas_from_oracle_mean", {})[key] = (analysis[key] - ref["mean"][key]) / ref["sd"][key]
+    return out
+
+
 def run_converge(args):
     """Time to convergence (every window at ln f < ln f_final) of full runs,
     one per seed: wall time of rewl_run from the created handle (set-up and
@@ -567,6 +592,7 @@ def run_converge(args):
                          "flips": s["flips"], "mean_flips_per_s": s["flips"] / secs,
                          "windows_done": s["windows_done"], "progress": [],
                          "analysis": analyse(r, p) if seed in finish else None})
+            runs[-1]["oracle"] = oracle_reference(args.workload, seed, runs[-1]["analysis"])
             r.close()
     for seed in ([] if args.concurrent else seeds):
         r = REWL(*WL.rewl_args(p, seed), spin_bits=p["spin_bits"])
@@ -586,6 +612,7 @@ def run_converge(args):
         runs.append({"seed": seed, "converged": bool(conv), "seconds": el, "rounds": s["rounds"],
                      "flips": s["flips"], "mean_flips_per_s": s["flips"] / el, "windows_done": s["windows_done"],
                      "progress": trace, "analysis": analyse(r, p) if conv else None})
+        runs[-1]["oracle"] = oracle_reference(args.workload, seed, runs[-1]["analysis"])
         print(json.dumps({"seed_done": runs[-1]}), flush=True)
         r.close()
     done = [x["seconds"] for x in runs if x["converged"]]
