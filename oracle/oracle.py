@@ -68,6 +68,16 @@ def lib():
         L.orc_set_round.restype = None
         L.orc_set_schedule.argtypes = [vp, i32]
         L.orc_set_schedule.restype = None
+        L.orc_production_start.argtypes = [vp, i32]
+        L.orc_production_start.restype = i32
+        L.orc_production_run.argtypes = [vp, i64]
+        L.orc_production_run.restype = i32
+        L.orc_get_heo.argtypes = [vp, vp]
+        L.orc_get_heo.restype = None
+        L.orc_majority.argtypes = [vp, i32, i32]
+        L.orc_majority.restype = i32
+        L.orc_obin.argtypes = [i32, i32, i32, i32]
+        L.orc_obin.restype = i32
         L.orc_walker_visited_all.argtypes = [vp, i32]
         L.orc_walker_visited_all.restype = i32
         L.ex_brute_force.argtypes = [i32, i32, vp]
@@ -208,6 +218,19 @@ class OracleREWL:
     def walker_visited_all(self, g):
         return bool(lib().orc_walker_visited_all(self._h, g))
 
+    def production_start(self, n_obins):
+        """Fixed weights from here on (ln f = 0), H(E,O) kept in n_obins classes."""
+        if lib().orc_production_start(self._h, n_obins):
+            raise ValueError("n_obins outside [1, N - ceil(N/q) + 1]")
+        self.n_obins = n_obins
+
+    def production_run(self, rounds):
+        if lib().orc_production_run(self._h, rounds):
+            raise RuntimeError("not in production")
+
+    def heo(self):
+        return self._get("orc_get_heo", (self.h, self.B, self.n_obins), np.uint64)
+
     def set_lng(self, v):
         a = np.ascontiguousarray(np.broadcast_to(v, (self.G, self.B)), dtype=np.float64)
         lib().orc_set_lng(self._h, _ptr(a))
@@ -270,3 +293,12 @@ class OracleREWL:
         if st:
             raise RuntimeError("join status %d" % st)
         return out
+
+
+def majority(sigma, q):
+    s = np.ascontiguousarray(sigma, dtype=np.uint8)
+    return int(lib().orc_majority(_ptr(s), s.size, q))
+
+
+def obin(n_max, N, q, n_obins):
+    return int(lib().orc_obin(n_max, N, q, n_obins))

@@ -190,6 +190,9 @@ typedef struct orc_rewl {
                         window -> highest -> lowest                            */
     int schedule;    /* ln f schedule: 0 halving (Sec. 2), 1 the 1/t rule     */
     uint8_t *phase;  /* [h] 1/t rule: 1 once the window follows ln f = 1/t   */
+    int production;  /* 1: fixed-weight production (ln f = 0, H(E,O) kept)   */
+    int n_obins;     /* classes of the observable O = majority count         */
+    uint64_t *heo;   /* [h][W+1][n_obins] production histogram H(E,O)        */
     int64_t round;   /* barriers (exchange rounds) completed                  */
     uint64_t xtried, xacc;
     int status;
@@ -202,7 +205,7 @@ void orc_destroy(orc_rewl *s)
     if (!s) return;
     free(s->e_lo); free(s->sigma); free(s->E); free(s->rep); free(s->t);
     free(s->lng); free(s->H); free(s->mask); free(s->lnf); free(s->iter); free(s->done);
-    free(s->rt_end); free(s->rt_trips); free(s->phase);
+    free(s->rt_end); free(s->rt_trips); free(s->phase); free(s->heo);
     free(s);
 }
 
@@ -322,6 +325,25 @@ orc_rewl *orc_create(int q, int L, int h, double overlap, int m, double lnf_fina
 /* ------------------------------------------------------------------------- */
 /* n standard WL steps of walker g at its window's ln f (Sec. 2, standard WL
  * paragraph; single-spin-flip proposals of Sec. 3.1). */
+/* The Potts observable of the production run: the majority count
+ * n_max = max over k of #{i : s_i = k}, in [ceil(N/q), N]. */
+int orc_majority(const uint8_t *sigma, int N, int q)
+{
+    int count[256] = {0};
+    for (int i = 0; i < N; ++i) count[sigma[i]] += 1;
+    int best = 0;
+    for (int k = 0; k < q; ++k)
+        if (count[k] > best) best = count[k];
+    return best;
+}
+
+/* Class of n_max among n_obins equal integer classes of [ceil(N/q), N]. */
+int orc_obin(int n_max, int N, int q, int n_obins)
+{
+    int lo = (N + q - 1) / q;
+    return (int)((int64_t)(n_max - lo) * n_obins / (N - lo + 1));
+}
+
 void orc_wl_steps(orc_rewl *s, int g, int64_t n)
 {
     int N = s->N, q = s->q, L = s->L;
@@ -350,6 +372,10 @@ void orc_wl_steps(orc_rewl *s, int g, int64_t n)
         }
         lg[E - lo] += lnf;
         Hg[E - lo] += 1u;
+        if (s->production) {
+            int o = orc_obin(orc_majority(sg, N, q), N, q, s->n_obins);
+            s->heo[((size_t)w * (s->W + 1) + (size_t)(E - lo)) * s->n_obins + o] += 1u;
+        }
     }
     s->E[g] = E;
     s->t[g] = t;
@@ -506,7 +532,7 @@ void orc_exchange(orc_rewl *s)
     uint8_t *tmp = (uint8_t *)malloc((size_t)N);
     uint32_t r[4];
     for (int a = (int)(s->round & 1); a + 1 < s->h; a += 2) {
-        if (s->done[a] || s->done[a + 1]) continue;
+        if (!s->production && (s->done[a] || s->done[a + 1])) continue;
         for (int k = 0; k < m; ++k) pi[k] = k;
         for (int i = m - 1; i >= 1; --i) {
             int n = m - 1 - i;
@@ -576,6 +602,51 @@ int orc_run(orc_rewl *s, int64_t max_rounds, int *converged)
     }
     if (converged) *converged = orc_all_done(s);
     return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Fixed-weight production run.  After g(E) has been estimated, the paper goes
+ * on sampling with the fixed weights 1/g(E) and measures distributions H(E,O)
+ * of observables (Sec. 3.2, for the lipid model; here O is the Potts majority
+ * count).  Every window keeps its walkers' ln g, and with ln f = 0 a WL step
+ * is exactly a Metropolis step with weights 1/g(E) restricted to the window;
+ * after each step H(E,O) of the window counts the walker's (E, class of O).
+ * A production round: K such steps of every walker of every window (finished
+ * or not), H cleared (it only counts the round's visits), replica exchange
+ * (Eq. 1, which keeps detailed balance of the fixed-weight ensembles) between
+ * every pair (a, a+1) with a = round (mod 2), round + 1.  No flatness check,
+ * merge or f-reduction. */
+int orc_production_start(orc_rewl *s, int n_obins)
+{
+    int lo = (s->N + s->q - 1) / s->q;
+    if (n_obins < 1 || n_obins > s->N - lo + 1) return ORC_ERR_ARG;
+    size_t n = (size_t)s->h * ((size_t)s->W + 1) * (size_t)n_obins;
+    free(s->heo);
+    s->heo = (uint64_t *)calloc(n, sizeof(uint64_t));
+    if (!s->heo) return ORC_ERR_NOMEM;
+    s->n_obins = n_obins;
+    s->production = 1;
+    for (int w = 0; w < s->h; ++w) s->lnf[w] = 0.0;
+    memset(s->H, 0, sizeof(uint32_t) * (size_t)s->h * s->m * ((size_t)s->W + 1));
+    return ORC_OK;
+}
+
+int orc_production_run(orc_rewl *s, int64_t rounds)
+{
+    if (!s->production) return ORC_ERR_STATE;
+    for (int64_t r = 0; r < rounds; ++r) {
+        for (int g = 0; g < s->h * s->m; ++g) orc_wl_steps(s, g, s->K);
+        memset(s->H, 0, sizeof(uint32_t) * (size_t)s->h * s->m * ((size_t)s->W + 1));
+        orc_exchange(s);
+        orc_track_round_trips(s);
+        s->round += 1;
+    }
+    return ORC_OK;
+}
+
+void orc_get_heo(const orc_rewl *s, uint64_t *o)
+{
+    if (s->heo) memcpy(o, s->heo, sizeof(uint64_t) * (size_t)s->h * ((size_t)s->W + 1) * (size_t)s->n_obins);
 }
 
 /* ------------------------------------------------------------------------- */

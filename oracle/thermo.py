@@ -30,6 +30,12 @@ Each function writes its definition out directly:
                        Also returns ln of the suppression of the transition
                        states: min over the energies between the peaks of
                        P(E) / P(peak) (10^-14 at L = 300, Sec. 3.1).
+  combine_heo / canonical_observable  the production run's H(E,O) (fixed
+                       weights 1/g(E), Sec. 3.2) summed over the windows that
+                       cover each energy gives the microcanonical distribution
+                       P(O|E) = H(E,O) / sum_O H(E,O); the canonical average is
+                       <O>(T) = sum_E g(E) exp(-E/T) <O>_E / sum_E g(E) exp(-E/T)
+                       over the energies with finite ln g and production counts.
   bootstrap            error estimate by resampling repeated runs (end of
                        Sec. 2): resample k takes runs draws[k, :], averages
                        their window pieces bin by bin (over the runs that
@@ -150,4 +156,32 @@ def bootstrap(q, N, e_lo, W, lng_runs, mask_runs, draws):
     for row in np.atleast_2d(draws):
         mean, mask = average_pieces(lng_runs, mask_runs, row)
         out.append(_orc.normalise(q, N, _orc.join_pieces(N, e_lo, W, mean, mask)))
+    return np.array(out)
+
+
+def combine_heo(heo, e_lo, N):
+    """H(E,O) of the windows (h, W+1, n_obins) summed onto the 2N+1 energies."""
+    heo = np.asarray(heo)
+    h, B, n_o = heo.shape
+    out = np.zeros((2 * N + 1, n_o), dtype=np.uint64)
+    for w in range(h):
+        b0 = int(e_lo[w]) + 2 * N
+        out[b0:b0 + B] += heo[w]
+    return out
+
+
+def canonical_observable(lng, counts, o_values, T):
+    """<O>(T) at each temperature of T from ln g and H(E,O) counts (2N+1, n_o)
+    whose class o stands for the value o_values[o]."""
+    lng = np.asarray(lng, dtype=np.float64)
+    N, E = _energies(lng)
+    counts = np.asarray(counts, dtype=np.float64)
+    tot = counts.sum(axis=1)
+    ok = np.isfinite(lng) & (tot > 0)
+    o_mean = (counts[ok] * np.asarray(o_values, dtype=np.float64)[None, :]).sum(axis=1) / tot[ok]
+    out = []
+    for t in np.atleast_1d(T):
+        a = lng[ok] - E[ok] / t
+        w = np.exp(a - a.max())
+        out.append((w * o_mean).sum() / w.sum())
     return np.array(out)
