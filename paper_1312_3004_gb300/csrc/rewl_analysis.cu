@@ -5,6 +5,7 @@
 // caller-supplied window pieces, and bootstrap resampling of repeated runs
 // (end of Sec. 2).  Host code: these act on at most 2N + 1 bins once per run,
 // after the sampling the GPU does.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -136,8 +137,7 @@ rewl_status rewl_specific_heat_peak(const double *lng, size_t len, double T_lo, 
         }
     }
     double a = T_lo + (k_best > 0 ? k_best - 1 : 0) * step;
-    double b = k_best < grid ? T_lo + (k_best + 1) * step : T_hi;
-    if (k_best + 1 == grid) b = T_hi;
+    double b = k_best + 1 < grid ? T_lo + (k_best + 1) * step : T_hi;
     const double r = 0.5 * (std::sqrt(5.0) - 1.0);
     double x1 = b - r * (b - a), x2 = a + r * (b - a);
     double c1 = c_at(x1), c2 = c_at(x2);
