@@ -30,7 +30,11 @@
  *     ln f < ln f_final, then replica exchange between windows (a, a+1) with
  *     a = round mod 2 and a random one-to-one matching of the m walkers;
  *   - joining at the bin where the two pieces' central-difference slopes
- *     agree best; normalisation sum_E g(E) = q^N.
+ *     agree best; normalisation sum_E g(E) = q^N;
+ *   - optional ln f schedule: the 1/t rule (Belardinelli & Pereyra), which
+ *     Sec. 2 admits as another valid WL update rule (orc_window_iterations);
+ *   - optional fixed-weight production with ln f = 0 and a histogram H(E,O)
+ *     of the majority count O (Sec. 3.2's production runs), orc_production_*.
  *
  * Floating point: IEEE binary64, round to nearest, no contraction (build with
  * -ffp-contract=off).  exp/log come from the C library.

@@ -14,6 +14,13 @@ CONFIGS = {
     # 10-state Potts L=20, 8 windows, 4 walkers, ln f_final 1e-8
     "potts10_L20": dict(q=10, L=20, h=8, overlap=0.75, m=4, lnf_final=1e-8, flatness=0.8,
                         exchange_interval=10_000, spin_bits=8),
+    # smaller sizes of the same layout: the finite-size series of Tc(L) (Sec. 3.1)
+    "potts10_L8": dict(q=10, L=8, h=8, overlap=0.75, m=4, lnf_final=1e-8, flatness=0.8,
+                       exchange_interval=10_000, spin_bits=8),
+    "potts10_L12": dict(q=10, L=12, h=8, overlap=0.75, m=4, lnf_final=1e-8, flatness=0.8,
+                        exchange_interval=10_000, spin_bits=8),
+    "potts10_L16": dict(q=10, L=16, h=8, overlap=0.75, m=4, lnf_final=1e-8, flatness=0.8,
+                        exchange_interval=10_000, spin_bits=8),
     # 10-state Potts L=80 (N=6400), 64 windows x 16 walkers = 1024 walkers, 4-bit spins
     "potts10_L80": dict(q=10, L=80, h=64, overlap=0.75, m=16, lnf_final=1e-8, flatness=0.8,
                         exchange_interval=10_000, spin_bits=4),
