@@ -533,7 +533,7 @@ def analyse(r, p):
     return out
 
 
-def oracle_reference(workload, seed, analysis):
+def oracle_reference(workload, seed, analysis, lng=None):
     """The oracle's converged values for this workload and seed, when stored
     (tests/golden/<workload>_converged.json, written by a script that runs
     only the oracle), with the oracle's mean and standard deviation over its
@@ -555,6 +555,13 @@ def oracle_reference(workload, seed, analysis):
     for key in ("c_peak_T", "c_peak", "Tc_equal_peak"):
         if analysis.get(key) is not None and ref["sd"][key] > 0:
             out.setdefault("sigmas_from_oracle_mean", {})[key] = (analysis[key] - ref["mean"][key]) / ref["sd"][key]
+    if lng is not None and "lng_mean" in ref:
+        # the run's normalised ln g against the oracle's seed mean, bin by bin, in
+        # units of the oracle's single-run standard deviation
+        z = [(x - m) / sd for x, m, sd in zip(lng, ref["lng_mean"], ref["lng_sd"]) if m is not None and sd > 0]
+        out["lng_bins"] = len(z)
+        out["lng_within_3sd"] = sum(abs(v) <= 3.0 for v in z) / max(1, len(z))
+        out["lng_max_abs_z"] = max((abs(v) for v in z), default=None)
     return out
 
 
@@ -592,7 +599,8 @@ def run_converge(args):
                          "flips": s["flips"], "mean_flips_per_s": s["flips"] / secs,
                          "windows_done": s["windows_done"], "progress": [],
                          "analysis": analyse(r, p) if seed in finish else None})
-            runs[-1]["oracle"] = oracle_reference(args.workload, seed, runs[-1]["analysis"])
+            runs[-1]["oracle"] = oracle_reference(args.workload, seed, runs[-1]["analysis"],
+                                                  r.lng() if seed in finish else None)
             r.close()
     for seed in ([] if args.concurrent else seeds):
         r = REWL(*WL.rewl_args(p, seed), spin_bits=p["spin_bits"])
@@ -612,7 +620,7 @@ def run_converge(args):
         runs.append({"seed": seed, "converged": bool(conv), "seconds": el, "rounds": s["rounds"],
                      "flips": s["flips"], "mean_flips_per_s": s["flips"] / el, "windows_done": s["windows_done"],
                      "progress": trace, "analysis": analyse(r, p) if conv else None})
-        runs[-1]["oracle"] = oracle_reference(args.workload, seed, runs[-1]["analysis"])
+        runs[-1]["oracle"] = oracle_reference(args.workload, seed, runs[-1]["analysis"], r.lng() if conv else None)
         print(json.dumps({"seed_done": runs[-1]}), flush=True)
         r.close()
     done = [x["seconds"] for x in runs if x["converged"]]

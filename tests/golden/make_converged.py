@@ -3,7 +3,9 @@ of a named 10-state Potts workload (paper_1312_3004_gb300/workloads.py) for a
 range of seeds, and the canonical analysis of each joined ln g (Sec. 3.1): the
 specific-heat maximum, the equal-peak temperature Tc(L) and the suppression of
 the transition states, searched within [0.8, 1.3] x 1/ln(1 + sqrt q); with the
-mean and sample standard deviation over the seeds.
+mean and sample standard deviation over the seeds of those numbers and of the
+joined, normalised ln g bin by bin (lng_mean, lng_sd; null where no
+configuration has that energy).
 
 Calls only the oracle (oracle/) and the workload table.  The seeds run in
 parallel processes, one per core but one.  A converged q = 10 run takes about
@@ -45,7 +47,7 @@ def one(job):
     T, c = TH.specific_heat_peak(lng, lo, hi)
     Tc, e_low, e_high, ln_sup = TH.equal_peak_temperature(lng, lo, hi)
     steps = int(o.t().sum())
-    return {"seed": seed, "rounds": int(o.round), "wl_steps": steps, "oracle_seconds": round(secs, 1),
+    return {"lng": [float(x) for x in lng], "seed": seed, "rounds": int(o.round), "wl_steps": steps, "oracle_seconds": round(secs, 1),
             "c_peak_T": T, "c_peak": c, "Tc_equal_peak": Tc, "E_peaks": [e_low, e_high],
             "ln_suppression": ln_sup}
 
@@ -75,6 +77,20 @@ def main():
         "T_range": "[0.8, 1.3] x 1/ln(1+sqrt(q))",
         "runs": runs,
     }
+    lngs = [r.pop("lng") for r in runs]
+    mean_b, sd_b = [], []
+    for b in range(len(lngs[0])):
+        v = [l[b] for l in lngs]
+        if any(math.isinf(x) for x in v):
+            assert all(math.isinf(x) for x in v)  # every run has the same support
+            mean_b.append(None)
+            sd_b.append(None)
+            continue
+        mu = sum(v) / len(v)
+        mean_b.append(mu)
+        sd_b.append(math.sqrt(sum((x - mu) ** 2 for x in v) / (len(v) - 1)) if len(v) > 1 else 0.0)
+    out["lng_mean"] = mean_b
+    out["lng_sd"] = sd_b
     for key in ("c_peak_T", "c_peak", "Tc_equal_peak", "ln_suppression"):
         v = [r[key] for r in runs]
         mean = sum(v) / len(v)

@@ -426,3 +426,20 @@ def test_one_window_has_no_round_trips():
     o = O.OracleREWL(2, 6, 1, 0.75, 3, 1e-3, 0.8, 300, 4)
     o.run(10)
     assert not o.rt_trips().any() and not o.rt_end().any()
+
+
+def test_every_walker_holds_every_replica_over_a_run():
+    """Fig. 7's diagnostic: over a run the exchanges carry every replica
+    through every walker slot (no empty bin in any slot's replica-id
+    histogram); with one window nothing is exchanged and each slot keeps its
+    own replica."""
+    o = O.OracleREWL(3, 6, 4, 0.75, 3, 1e-5, 0.8, 1000, 2)
+    G = o.G
+    seen = np.zeros((G, G), dtype=bool)
+    while not o.all_done():
+        o.run(1)
+        seen[np.arange(G), o.rep()] = True
+    assert seen.all()
+    one = O.OracleREWL(3, 6, 1, 0.75, 3, 1e-3, 0.8, 1000, 2)
+    one.run(0)
+    assert np.array_equal(one.rep(), np.arange(3))
