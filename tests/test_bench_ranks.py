@@ -90,3 +90,26 @@ def test_clock_record_keeps_the_timed_region_and_every_throttle_reason():
     hot = bench.summarize_clocks([row(t0, 1500, ("Active", "Not Active", "Not Active", "Not Active"))], None)
     assert hot["reasons"] == ["hw_slowdown"]
     assert bench.summarize_clocks([], None)["reasons"] == ["no samples"]
+
+
+def test_converge_report_compares_with_the_oracle_values():
+    """bench.py --converge compares a converged run with the oracle's stored
+    run of the same seed and with the oracle's seed mean, bin by bin."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    import bench
+
+    with open(os.path.join(root, "tests", "golden", "potts10_L8_converged.json")) as f:
+        ref = json.load(f)
+    r1 = ref["runs"][0]
+    same = {k: r1[k] for k in ("c_peak_T", "c_peak", "Tc_equal_peak", "E_peaks")}
+    lng = [m if m is not None else float("-inf") for m in ref["lng_mean"]]
+    out = bench.oracle_reference("potts10_L8", r1["seed"], same, lng)
+    assert out["same_as_oracle"] is True
+    assert out["oracle_seeds"] == len(ref["runs"])
+    assert out["lng_within_3sd"] == 1.0 and out["lng_max_abs_z"] == 0.0
+    assert out["lng_bins"] == sum(m is not None for m in ref["lng_mean"])
+    moved = dict(same, c_peak_T=same["c_peak_T"] * 1.001)
+    assert bench.oracle_reference("potts10_L8", r1["seed"], moved, None)["same_as_oracle"] is False
+    assert bench.oracle_reference("potts10_L8", 99, same, None).get("oracle_same_seed") is None
+    assert bench.oracle_reference("no_such_workload", 1, same, None) is None
