@@ -83,6 +83,7 @@ Moments moments(const Bins &x, int N, double T) {
 extern "C" {
 
 rewl_status rewl_canonical(const double *lng, size_t len, const double *T, size_t nT, double *out) {
+    REWL_API_TRY
     int N;
     rewl_status st = check_lng(lng, len, &N);
     if (st) return st;
@@ -98,9 +99,11 @@ rewl_status rewl_canonical(const double *lng, size_t len, const double *T, size_
         out[4 * i + 3] = m.s;
     }
     return REWL_OK;
+    REWL_API_CATCH
 }
 
 rewl_status rewl_canonical_distribution(const double *lng, size_t len, double T, double *out) {
+    REWL_API_TRY
     int N;
     rewl_status st = check_lng(lng, len, &N);
     if (st) return st;
@@ -112,10 +115,12 @@ rewl_status rewl_canonical_distribution(const double *lng, size_t len, double T,
     for (size_t b = 0; b < len; ++b)
         out[b] = lng[b] == -INFINITY ? 0.0 : std::exp((lng[b] - ((double)b - 2.0 * N) / T) - top);
     return REWL_OK;
+    REWL_API_CATCH
 }
 
 rewl_status rewl_specific_heat_peak(const double *lng, size_t len, double T_lo, double T_hi, double *T_peak,
                                     double *c_peak) {
+    REWL_API_TRY
     int N;
     rewl_status st = check_lng(lng, len, &N);
     if (st) return st;
@@ -164,10 +169,12 @@ rewl_status rewl_specific_heat_peak(const double *lng, size_t len, double T_lo, 
     *T_peak = T;
     *c_peak = c;
     return REWL_OK;
+    REWL_API_CATCH
 }
 
 rewl_status rewl_equal_peak_temperature(const double *lng, size_t len, double T_lo, double T_hi, double *Tc,
                                         int *e_low, int *e_high, double *ln_suppression) {
+    REWL_API_TRY
     int N;
     rewl_status st = check_lng(lng, len, &N);
     if (st) return st;
@@ -211,15 +218,18 @@ rewl_status rewl_equal_peak_temperature(const double *lng, size_t len, double T_
     if (e_high) *e_high = (int)x.E[best_b];
     if (ln_suppression) *ln_suppression = low - (x.lg[best_a] - x.E[best_a] / best_T);
     return REWL_OK;
+    REWL_API_CATCH
 }
 
 rewl_status rewl_ising_energy(int L, int b, long long *e_ising) {
+    REWL_API_TRY
     if (!e_ising) return fail(REWL_ERR_ARG, "NULL output");
     if (L < 3 || L > 1024) return fail(REWL_ERR_ARG, "L=%d outside [3, 1024]", L);
     const long long N = (long long)L * L;
     if (b < 0 || b > 2 * N) return fail(REWL_ERR_ARG, "bin %d outside [0, 2N]", b);
     *e_ising = 2LL * b - 2LL * N;
     return REWL_OK;
+    REWL_API_CATCH
 }
 
 }  // extern "C"
@@ -246,6 +256,7 @@ extern "C" {
 
 rewl_status rewl_join(int q, int L, int h, int W, const int *e_lo, const double *lng_w, const unsigned char *mask_w,
                       double *out, size_t len) {
+    REWL_API_TRY
     rewl_status st = check_pieces(q, L, h, W, e_lo, len);
     if (st) return st;
     if (!lng_w || !mask_w || !out) return fail(REWL_ERR_ARG, "NULL argument");
@@ -258,10 +269,12 @@ rewl_status rewl_join(int q, int L, int h, int W, const int *e_lo, const double 
     if (st) return st;
     rewl::host::normalise_total(q, N, out, 2 * N + 1);
     return REWL_OK;
+    REWL_API_CATCH
 }
 
 rewl_status rewl_bootstrap(int q, int L, int h, int W, const int *e_lo, int runs, const double *lng_runs,
                            const unsigned char *mask_runs, int resamples, const int *draws, double *out, size_t len) {
+    REWL_API_TRY
     rewl_status st = check_pieces(q, L, h, W, e_lo, len);
     if (st) return st;
     if (runs < 1 || resamples < 0) return fail(REWL_ERR_ARG, "runs=%d or resamples=%d out of range", runs, resamples);
@@ -297,6 +310,7 @@ rewl_status rewl_bootstrap(int q, int L, int h, int W, const int *e_lo, int runs
         rewl::host::normalise_total(q, N, o, 2 * N + 1);
     }
     return REWL_OK;
+    REWL_API_CATCH
 }
 
 }  // extern "C"

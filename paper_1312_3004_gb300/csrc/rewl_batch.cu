@@ -140,10 +140,13 @@ void destroy_batch(rewl_batch_s *b) {
 extern "C" {
 
 rewl_status rewl_batch_create(const rewl_params *jobs, int n, int spin_bits, rewl_batch_t *out) {
+    REWL_API_TRY
     return rewl_batch_create_ext(jobs, n, spin_bits, 0, out);
+    REWL_API_CATCH
 }
 
 rewl_status rewl_batch_create_ext(const rewl_params *jobs, int n, int spin_bits, int lanes, rewl_batch_t *out) {
+    REWL_API_TRY
     if (!jobs || !out || n < 1) return fail(REWL_ERR_ARG, "NULL argument or n < 1");
     if (lanes != 0 && lanes != 1 && lanes != 32) return fail(REWL_ERR_ARG, "lanes %d not 0, 1 or 32", lanes);
     *out = nullptr;
@@ -279,30 +282,38 @@ rewl_status rewl_batch_create_ext(const rewl_params *jobs, int n, int spin_bits,
     if (st) return cleanup(st);
     *out = b;
     return REWL_OK;
+    REWL_API_CATCH
 }
 
 void rewl_batch_destroy(rewl_batch_t b) { destroy_batch(b); }
 
 rewl_status rewl_batch_set_stream(rewl_batch_t b, void *stream) {
+    REWL_API_TRY
     if (!b) return fail(REWL_ERR_ARG, "NULL batch");
     BATCH_CUDA(cudaStreamSynchronize(b->stream));
     b->stream = stream ? (cudaStream_t)stream : b->own_stream;
     for (rewl_s *h : b->inst) h->stream = b->stream;
     return REWL_OK;
+    REWL_API_CATCH
 }
 
 rewl_status rewl_batch_run_async(rewl_batch_t b, long long rounds) {
+    REWL_API_TRY
     if (!b) return fail(REWL_ERR_ARG, "NULL batch");
     if (rounds < 0) return fail(REWL_ERR_ARG, "rounds < 0");
     return enqueue_batch_rounds(b, rounds);
+    REWL_API_CATCH
 }
 
 rewl_status rewl_batch_sync(rewl_batch_t b, int *n_converged) {
+    REWL_API_TRY
     if (!b) return fail(REWL_ERR_ARG, "NULL batch");
     return read_batch_status(b, n_converged);
+    REWL_API_CATCH
 }
 
 rewl_status rewl_batch_run(rewl_batch_t b, long long max_rounds, int *n_converged) {
+    REWL_API_TRY
     const rewl::host::Range range("rewl_batch_run");
     if (!b) return fail(REWL_ERR_ARG, "NULL batch");
     const int n = (int)b->inst.size();
@@ -317,16 +328,20 @@ rewl_status rewl_batch_run(rewl_batch_t b, long long max_rounds, int *n_converge
     }
     if (n_converged) *n_converged = done;
     return st;
+    REWL_API_CATCH
 }
 
 rewl_status rewl_batch_instance(rewl_batch_t b, int i, rewl_t *view) {
+    REWL_API_TRY
     if (!b || !view) return fail(REWL_ERR_ARG, "NULL argument");
     if (i < 0 || i >= (int)b->inst.size()) return fail(REWL_ERR_ARG, "instance %d outside [0, %zu)", i, b->inst.size());
     *view = b->inst[(size_t)i];
     return REWL_OK;
+    REWL_API_CATCH
 }
 
 rewl_status rewl_batch_info(rewl_batch_t b, int *n_instances, long long *walkers, size_t *device_bytes) {
+    REWL_API_TRY
     if (!b) return fail(REWL_ERR_ARG, "NULL batch");
     long long w = 0;
     for (rewl_s *h : b->inst) w += h->M.G;
@@ -334,9 +349,11 @@ rewl_status rewl_batch_info(rewl_batch_t b, int *n_instances, long long *walkers
     if (walkers) *walkers = w;
     if (device_bytes) *device_bytes = b->dbytes;
     return REWL_OK;
+    REWL_API_CATCH
 }
 
 rewl_status rewl_batch_stats(rewl_batch_t b, rewl_stats *s) {
+    REWL_API_TRY
     if (!b || !s) return fail(REWL_ERR_ARG, "NULL argument");
     int done = 0;
     rewl_status st = read_batch_status(b, &done);
@@ -357,6 +374,7 @@ rewl_status rewl_batch_stats(rewl_batch_t b, rewl_stats *s) {
     s->windows_done = done;  // instances, for a batch
     s->converged = done == (int)b->inst.size() ? 1 : 0;
     return st;
+    REWL_API_CATCH
 }
 
 }  // extern "C"

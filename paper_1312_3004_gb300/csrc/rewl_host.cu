@@ -380,6 +380,7 @@ const char *rewl_last_error(void) { return g_last_error.c_str(); }
 const char *rewl_version(void) { return "rewl-gb300 0.1 (sm_103a)"; }
 
 rewl_status rewl_create_ext(const rewl_params *prm, int spin_bits, rewl_t *out) {
+    REWL_API_TRY
     const rewl::host::Range range("rewl_create");
     if (!prm || !out) return fail(REWL_ERR_ARG, "NULL argument");
     *out = nullptr;
@@ -408,10 +409,12 @@ rewl_status rewl_create_ext(const rewl_params *prm, int spin_bits, rewl_t *out) 
     if (st) return cleanup(st);
     *out = h;
     return REWL_OK;
+    REWL_API_CATCH
 }
 
 rewl_status rewl_create(int q, int L, int h, double overlap, int m, double lnf_final, double flatness,
                         long long exchange_interval, unsigned long long seed, rewl_t *out) {
+    REWL_API_TRY
     rewl_params p;
     p.q = q;
     p.L = L;
@@ -423,6 +426,7 @@ rewl_status rewl_create(int q, int L, int h, double overlap, int m, double lnf_f
     p.exchange_interval = exchange_interval;
     p.seed = seed;
     return rewl_create_ext(&p, 0, out);
+    REWL_API_CATCH
 }
 
 void rewl_set_allocator(void *(*alloc)(size_t bytes, void *ctx), void (*free_fn)(void *ptr, void *ctx), void *ctx) {
@@ -440,21 +444,26 @@ void rewl_destroy(rewl_t h) {
 }
 
 rewl_status rewl_set_stream(rewl_t h, void *stream) {
+    REWL_API_TRY
     if (h && !h->owns) return fail(REWL_ERR_STATE, "this instance belongs to a batch: run the batch");
     if (!h) return fail(REWL_ERR_ARG, "NULL handle");
     REWL_CUDA(cudaStreamSynchronize(h->stream));
     h->stream = stream ? (cudaStream_t)stream : h->own_stream;
     return REWL_OK;
+    REWL_API_CATCH
 }
 
 rewl_status rewl_run_async(rewl_t h, long long rounds) {
+    REWL_API_TRY
     if (h && !h->owns) return fail(REWL_ERR_STATE, "this instance belongs to a batch: run the batch");
     if (!h) return fail(REWL_ERR_ARG, "NULL handle");
     if (rounds < 0) return fail(REWL_ERR_ARG, "rounds < 0");
     return enqueue_rounds(h, rounds);
+    REWL_API_CATCH
 }
 
 rewl_status rewl_run_phase(rewl_t h, int phase) {
+    REWL_API_TRY
     const rewl::host::Range range(phase == REWL_PHASE_SWEEP ? "rewl_phase_sweep"
                                   : phase == REWL_PHASE_CHECK ? "rewl_phase_check"
                                                               : "rewl_phase_exchange");
@@ -467,9 +476,11 @@ rewl_status rewl_run_phase(rewl_t h, int phase) {
     default: return fail(REWL_ERR_ARG, "unknown phase %d", phase);
     }
     return REWL_OK;
+    REWL_API_CATCH
 }
 
 rewl_status rewl_set_option(rewl_t h, int option, long long value) {
+    REWL_API_TRY
     if (h && !h->owns) return fail(REWL_ERR_STATE, "this instance belongs to a batch: run the batch");
     if (!h) return fail(REWL_ERR_ARG, "NULL handle");
     int kind = h->plan.kind, lanes = h->plan.lanes, lat_mode = h->lat_mode;
@@ -509,9 +520,11 @@ rewl_status rewl_set_option(rewl_t h, int option, long long value) {
         h->graph = nullptr;
     }
     return build_graph(h);
+    REWL_API_CATCH
 }
 
 rewl_status rewl_get_option(rewl_t h, int option, long long *value) {
+    REWL_API_TRY
     if (!h || !value) return fail(REWL_ERR_ARG, "NULL argument");
     if (option == REWL_OPT_SWEEP_KERNEL) *value = h->plan.kind == rewl::SWEEP_FAST ? 0 : 1;
     else if (option == REWL_OPT_LANES) *value = h->plan.lanes;
@@ -521,16 +534,20 @@ rewl_status rewl_get_option(rewl_t h, int option, long long *value) {
     else if (option == REWL_OPT_SCHEDULE) *value = h->M.schedule;
     else return fail(REWL_ERR_ARG, "unknown option %d", option);
     return REWL_OK;
+    REWL_API_CATCH
 }
 
 rewl_status rewl_sync(rewl_t h, int *converged) {
+    REWL_API_TRY
     if (!h) return fail(REWL_ERR_ARG, "NULL handle");
     rewl_status st = read_ctl(h);
     if (converged) *converged = h->h_ctl->all_done ? 1 : 0;
     return st;
+    REWL_API_CATCH
 }
 
 rewl_status rewl_run(rewl_t h, long long max_rounds, int *converged) {
+    REWL_API_TRY
     const rewl::host::Range range("rewl_run");
     if (h && !h->owns) return fail(REWL_ERR_STATE, "this instance belongs to a batch: run the batch");
     if (!h) return fail(REWL_ERR_ARG, "NULL handle");
@@ -569,9 +586,11 @@ rewl_status rewl_run(rewl_t h, long long max_rounds, int *converged) {
     }
     if (converged) *converged = h->h_ctl->all_done ? 1 : 0;
     return st;
+    REWL_API_CATCH
 }
 
 rewl_status rewl_get_window_lng(rewl_t h, int w, double *out, size_t len, int *e_lo) {
+    REWL_API_TRY
     if (!h || !out) return fail(REWL_ERR_ARG, "NULL argument");
     if (w < 0 || w >= h->M.h) return fail(REWL_ERR_ARG, "window %d outside [0, %d)", w, h->M.h);
     if (len != (size_t)h->M.B) return fail(REWL_ERR_ARG, "len %zu != W + 1 = %d", len, h->M.B);
@@ -579,9 +598,11 @@ rewl_status rewl_get_window_lng(rewl_t h, int w, double *out, size_t len, int *e
     REWL_CUDA(cudaStreamSynchronize(h->stream));
     if (e_lo) *e_lo = h->e_lo[(size_t)w];
     return REWL_OK;
+    REWL_API_CATCH
 }
 
 rewl_status rewl_get_lng(rewl_t h, double *out, size_t len, int partial) {
+    REWL_API_TRY
     if (!h || !out) return fail(REWL_ERR_ARG, "NULL argument");
     const Model &M = h->M;
     if (len != (size_t)(2 * M.N + 1)) return fail(REWL_ERR_ARG, "len %zu != 2N + 1 = %d", len, 2 * M.N + 1);
@@ -599,9 +620,11 @@ rewl_status rewl_get_lng(rewl_t h, double *out, size_t len, int partial) {
     if (st) return st;
     normalise_total(M.q, M.N, out, 2 * M.N + 1);
     return REWL_OK;
+    REWL_API_CATCH
 }
 
 rewl_status rewl_get_info(rewl_t h, rewl_info *info) {
+    REWL_API_TRY
     if (!h || !info) return fail(REWL_ERR_ARG, "NULL argument");
     info->N = h->M.N;
     info->W = h->M.W;
@@ -609,9 +632,11 @@ rewl_status rewl_get_info(rewl_t h, rewl_info *info) {
     info->spin_bits = h->M.bits;
     info->device_bytes = h->dbytes;
     return REWL_OK;
+    REWL_API_CATCH
 }
 
 rewl_status rewl_get_stats(rewl_t h, rewl_stats *s) {
+    REWL_API_TRY
     if (!h || !s) return fail(REWL_ERR_ARG, "NULL argument");
     std::vector<double> lnf((size_t)h->M.h);
     std::vector<uint8_t> done((size_t)h->M.h);
@@ -637,6 +662,7 @@ rewl_status rewl_get_stats(rewl_t h, rewl_stats *s) {
     }
     s->converged = c.all_done ? 1 : 0;
     return st;
+    REWL_API_CATCH
 }
 
 static rewl_status field_geometry(rewl_t h, int field, void **dev, size_t *bytes) {
@@ -663,6 +689,7 @@ static rewl_status field_geometry(rewl_t h, int field, void **dev, size_t *bytes
 }
 
 rewl_status rewl_get_field(rewl_t h, int field, void *out, size_t bytes) {
+    REWL_API_TRY
     if (!h || !out) return fail(REWL_ERR_ARG, "NULL argument");
     void *dev;
     size_t need;
@@ -690,9 +717,11 @@ rewl_status rewl_get_field(rewl_t h, int field, void *out, size_t bytes) {
     }
     REWL_CUDA(cudaStreamSynchronize(h->stream));
     return REWL_OK;
+    REWL_API_CATCH
 }
 
 rewl_status rewl_set_field(rewl_t h, int field, const void *in, size_t bytes) {
+    REWL_API_TRY
     if (!h || !in) return fail(REWL_ERR_ARG, "NULL argument");
     if (field == REWL_FIELD_ELO || field == REWL_FIELD_REPLICA || field == REWL_FIELD_ENERGY)
         return fail(REWL_ERR_ARG, "field %d is read-only", field);
@@ -716,9 +745,11 @@ rewl_status rewl_set_field(rewl_t h, int field, const void *in, size_t bytes) {
     }
     REWL_CUDA(cudaStreamSynchronize(h->stream));
     return REWL_OK;
+    REWL_API_CATCH
 }
 
 rewl_status rewl_save(rewl_t h, void *buf, size_t *len) {
+    REWL_API_TRY
     if (!h || !len) return fail(REWL_ERR_ARG, "NULL argument");
     size_t payload = 0;
     for (auto &p : h->parts) payload += p.bytes;
@@ -748,9 +779,11 @@ rewl_status rewl_save(rewl_t h, void *buf, size_t *len) {
     std::memcpy(buf, &hd, sizeof hd);
     *len = need;
     return REWL_OK;
+    REWL_API_CATCH
 }
 
 rewl_status rewl_load(rewl_t h, const void *buf, size_t len) {
+    REWL_API_TRY
     if (!h || !buf) return fail(REWL_ERR_ARG, "NULL argument");
     if (len < sizeof(SaveHeader)) return fail(REWL_ERR_ARG, "blob too short");
     SaveHeader hd;
@@ -775,6 +808,7 @@ rewl_status rewl_load(rewl_t h, const void *buf, size_t len) {
     }
     REWL_CUDA(cudaStreamSynchronize(h->stream));
     return read_ctl(h);
+    REWL_API_CATCH
 }
 
 }  // extern "C"

@@ -1,12 +1,25 @@
 // rewl_host_internal.hpp -- host-side instance record shared by the
 // single-instance driver (rewl_host.cu) and the batch engine (rewl_batch.cu).
 #pragma once
+#include <new>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
 
 #include "rewl.h"
 #include "rewl_internal.cuh"
+
+// Every entry point of the C ABI returns a status and lets no C++ exception
+// (a failed host allocation inside a standard container) cross the ABI.
+#define REWL_API_TRY try {
+#define REWL_API_CATCH                                                                     \
+    }                                                                                      \
+    catch (const std::bad_alloc &) {                                                       \
+        return rewl::host::fail(REWL_ERR_NOMEM, "host memory exhausted");                  \
+    }                                                                                      \
+    catch (...) {                                                                          \
+        return rewl::host::fail(REWL_ERR_STATE, "unexpected host error");                 \
+    }
 
 namespace rewl {
 namespace host {

@@ -271,6 +271,7 @@ rewl_status admit(rewl_server_s *s) {
 extern "C" {
 
 rewl_status rewl_server_create(size_t pool_bytes, int max_jobs, rewl_server_t *out) {
+    REWL_API_TRY
     if (!out || pool_bytes < 4096 || max_jobs < 1) return fail(REWL_ERR_ARG, "pool_bytes < 4096 or max_jobs < 1");
     *out = nullptr;
     rewl_server_s *s = new rewl_server_s();
@@ -297,6 +298,7 @@ rewl_status rewl_server_create(size_t pool_bytes, int max_jobs, rewl_server_t *o
     for (int i = max_jobs - 1; i >= 0; --i) s->free_slots.push_back(i);
     *out = s;
     return REWL_OK;
+    REWL_API_CATCH
 }
 
 void rewl_server_destroy(rewl_server_t s) {
@@ -313,6 +315,7 @@ void rewl_server_destroy(rewl_server_t s) {
 }
 
 rewl_status rewl_server_submit(rewl_server_t s, const rewl_params *p, int spin_bits, long long *job_id) {
+    REWL_API_TRY
     if (!s || !p) return fail(REWL_ERR_ARG, "NULL argument");
     rewl_s probe;
     rewl_status st = rewl::host::prepare_instance(&probe, *p, spin_bits, 32);
@@ -328,9 +331,11 @@ rewl_status rewl_server_submit(rewl_server_t s, const rewl_params *p, int spin_b
     s->queue.push_back(j.id);
     if (job_id) *job_id = j.id;
     return REWL_OK;
+    REWL_API_CATCH
 }
 
 rewl_status rewl_server_step(rewl_server_t s, long long rounds, int *n_running, int *n_queued) {
+    REWL_API_TRY
     const rewl::host::Range range("rewl_server_step");
     if (!s) return fail(REWL_ERR_ARG, "NULL server");
     if (rounds < 1) return fail(REWL_ERR_ARG, "rounds < 1");
@@ -382,17 +387,21 @@ rewl_status rewl_server_step(rewl_server_t s, long long rounds, int *n_running, 
     if (n_running) *n_running = (int)s->running.size();
     if (n_queued) *n_queued = (int)s->queue.size();
     return REWL_OK;
+    REWL_API_CATCH
 }
 
 rewl_status rewl_server_poll(rewl_server_t s, long long job_id, int *state) {
+    REWL_API_TRY
     if (!s || !state) return fail(REWL_ERR_ARG, "NULL argument");
     auto it = s->jobs.find(job_id);
     if (it == s->jobs.end()) return fail(REWL_ERR_ARG, "unknown job %lld", job_id);
     *state = it->second.state;
     return REWL_OK;
+    REWL_API_CATCH
 }
 
 rewl_status rewl_server_result(rewl_server_t s, long long job_id, double *out, size_t len) {
+    REWL_API_TRY
     if (!s || !out) return fail(REWL_ERR_ARG, "NULL argument");
     auto it = s->jobs.find(job_id);
     if (it == s->jobs.end()) return fail(REWL_ERR_ARG, "unknown job %lld", job_id);
@@ -403,9 +412,11 @@ rewl_status rewl_server_result(rewl_server_t s, long long job_id, double *out, s
     if (len != j.result.size()) return fail(REWL_ERR_ARG, "len %zu != 2N + 1 = %zu", len, j.result.size());
     std::memcpy(out, j.result.data(), len * sizeof(double));
     return REWL_OK;
+    REWL_API_CATCH
 }
 
 rewl_status rewl_server_job_info(rewl_server_t s, long long job_id, double *times, long long *counts) {
+    REWL_API_TRY
     if (!s) return fail(REWL_ERR_ARG, "NULL server");
     auto it = s->jobs.find(job_id);
     if (it == s->jobs.end()) return fail(REWL_ERR_ARG, "unknown job %lld", job_id);
@@ -421,9 +432,11 @@ rewl_status rewl_server_job_info(rewl_server_t s, long long job_id, double *time
         counts[2] = (long long)j.bytes;
     }
     return REWL_OK;
+    REWL_API_CATCH
 }
 
 rewl_status rewl_server_cancel(rewl_server_t s, long long job_id) {
+    REWL_API_TRY
     if (!s) return fail(REWL_ERR_ARG, "NULL server");
     auto it = s->jobs.find(job_id);
     if (it == s->jobs.end()) return fail(REWL_ERR_ARG, "unknown job %lld", job_id);
@@ -438,9 +451,11 @@ rewl_status rewl_server_cancel(rewl_server_t s, long long job_id) {
         s->tables_dirty = true;
     }
     return REWL_OK;
+    REWL_API_CATCH
 }
 
 rewl_status rewl_server_info(rewl_server_t s, long long *counts, size_t *pool_free) {
+    REWL_API_TRY
     if (!s) return fail(REWL_ERR_ARG, "NULL server");
     if (counts) {
         long long q = 0, r = 0, d = 0, f = 0;
@@ -464,6 +479,7 @@ rewl_status rewl_server_info(rewl_server_t s, long long *counts, size_t *pool_fr
         *pool_free = fr;
     }
     return REWL_OK;
+    REWL_API_CATCH
 }
 
 }  // extern "C"
