@@ -355,8 +355,14 @@ rewl_status rewl_server_result(rewl_server_t s, long long job_id, double *out, s
 rewl_status rewl_server_job_info(rewl_server_t s, long long job_id, double *times, long long *counts);
 /* Cancel a queued or running job (its memory returns to the pool). */
 rewl_status rewl_server_cancel(rewl_server_t s, long long job_id);
+/* Forget a finished, failed or cancelled job: its record and kept result are
+ * freed, and the id becomes unknown (a long-running server calls this once it
+ * has read a result).  Errors: REWL_ERR_ARG (unknown job), REWL_ERR_STATE (the
+ * job is queued or running). */
+rewl_status rewl_server_release(rewl_server_t s, long long job_id);
 /* counts (may be NULL): [queued, running, done, failed or cancelled, rounds
- * stepped, WL proposals]; *pool_free (may be NULL): free pool bytes. */
+ * stepped, WL proposals] (done / failed / cancelled: jobs not yet released);
+ * *pool_free (may be NULL): free pool bytes. */
 rewl_status rewl_server_info(rewl_server_t s, long long *counts, size_t *pool_free);
 /* Release the server, its pool and every job.  NULL is ignored. */
 void rewl_server_destroy(rewl_server_t s);

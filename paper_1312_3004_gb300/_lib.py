@@ -109,9 +109,11 @@ def load():
     L.rewl_server_result.argtypes = [H, ll, vp, sz]
     L.rewl_server_job_info.argtypes = [H, ll, vp, vp]
     L.rewl_server_cancel.argtypes = [H, ll]
+    L.rewl_server_release.argtypes = [H, ll]
     L.rewl_server_info.argtypes = [H, vp, C.POINTER(C.c_size_t)]
     for name in ("rewl_server_create", "rewl_server_submit", "rewl_server_step", "rewl_server_poll",
-                 "rewl_server_result", "rewl_server_job_info", "rewl_server_cancel", "rewl_server_info"):
+                 "rewl_server_result", "rewl_server_job_info", "rewl_server_cancel", "rewl_server_release",
+                 "rewl_server_info"):
         getattr(L, name).restype = st
     L.rewl_server_destroy.argtypes = [H]
     L.rewl_server_destroy.restype = None

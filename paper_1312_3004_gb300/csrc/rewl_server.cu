@@ -454,6 +454,19 @@ rewl_status rewl_server_cancel(rewl_server_t s, long long job_id) {
     REWL_API_CATCH
 }
 
+rewl_status rewl_server_release(rewl_server_t s, long long job_id) {
+    REWL_API_TRY
+    if (!s) return fail(REWL_ERR_ARG, "NULL server");
+    auto it = s->jobs.find(job_id);
+    if (it == s->jobs.end()) return fail(REWL_ERR_ARG, "unknown job %lld", job_id);
+    const int st = it->second.state;
+    if (st == JOB_QUEUED || st == JOB_RUNNING)
+        return fail(REWL_ERR_STATE, "job %lld is still %s", job_id, st == JOB_QUEUED ? "queued" : "running");
+    s->jobs.erase(it);
+    return REWL_OK;
+    REWL_API_CATCH
+}
+
 rewl_status rewl_server_info(rewl_server_t s, long long *counts, size_t *pool_free) {
     REWL_API_TRY
     if (!s) return fail(REWL_ERR_ARG, "NULL server");

@@ -306,6 +306,10 @@ class Server:
     def cancel(self, job):
         check(self._L.rewl_server_cancel(self._h, job))
 
+    def release(self, job):
+        """Forget a finished (or failed / cancelled) job and its kept result."""
+        check(self._L.rewl_server_release(self._h, job))
+
     def info(self):
         c = np.zeros(6, dtype=np.int64)
         f = C.c_size_t(0)

@@ -106,6 +106,7 @@ def test_server_arguments_are_checked_before_any_device_work():
     p = params()
     assert lib.rewl_server_submit(None, C.byref(p), 0, C.byref(jid)) == 1
     assert lib.rewl_server_step(None, 1, None, None) == 1
+    assert lib.rewl_server_release(None, 1) == 1
     lib.rewl_server_destroy(None)
 
 

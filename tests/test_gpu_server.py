@@ -91,3 +91,27 @@ def test_cancel_and_errors():
     big = dict(j, L=200, h=4)
     with pytest.raises(RewlError):
         srv.submit(**big)  # larger than the pool
+
+
+def test_release_forgets_finished_jobs():
+    srv = Server(pool_bytes=64 << 20, max_jobs=4)
+    j = small_jobs()[4]
+    jid = srv.submit(**j)
+    with pytest.raises(RewlError):
+        srv.release(jid)  # queued: not finished
+    ticks = 0
+    while srv.poll(jid) != "done":
+        srv.step(rounds=4)
+        ticks += 1
+        assert ticks < 100000
+    assert same(srv.result(jid), alone_result(j))
+    done_before = srv.info()["done"]
+    srv.release(jid)
+    assert srv.info()["done"] == done_before - 1
+    with pytest.raises(RewlError):
+        srv.poll(jid)  # the id is unknown now
+    with pytest.raises(RewlError):
+        srv.release(jid)
+    other = srv.submit(**j)
+    srv.cancel(other)
+    srv.release(other)
