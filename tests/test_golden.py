@@ -61,3 +61,69 @@ def test_stored_exact_densities_of_states():
         assert again == g, key
     # the two methods agree where both apply
     assert O.exact_counts_tm(2, 4) == [int(c) for c in d["brute_q2_L4"]["counts"]]
+
+
+TC_Q10 = 1.0 / math.log(1.0 + math.sqrt(10.0))
+
+
+def _check_converged_file(name, seeds):
+    d = load(name + "_converged.json")
+    runs = d["runs"]
+    assert [r["seed"] for r in runs] == list(seeds)
+    for key in ("c_peak_T", "c_peak", "Tc_equal_peak", "ln_suppression"):
+        v = [r[key] for r in runs]
+        mean = sum(v) / len(v)
+        sd = math.sqrt(sum((x - mean) ** 2 for x in v) / (len(v) - 1))
+        assert math.isclose(d["mean"][key], mean, rel_tol=1e-12)
+        assert math.isclose(d["sd"][key], sd, rel_tol=1e-9, abs_tol=1e-300)
+    p = WL.params(name)
+    N = p["L"] ** 2
+    assert len(d["lng_mean"]) == len(d["lng_sd"]) == 2 * N + 1
+    # the support is the set of energies that exist: none of 1, 2, 3, 5 broken bonds
+    assert [d["lng_mean"][k] is None for k in range(8)] == [False, True, True, True, False, True, False, False]
+    # normalised: ln g(ground) = ln q up to the run-to-run error, sum g = q^N
+    assert abs(d["lng_mean"][0] - math.log(p["q"])) < 5 * d["lng_sd"][0] + 0.05
+    top = max(x for x in d["lng_mean"] if x is not None)
+    s = sum(math.exp(x - top) for x in d["lng_mean"] if x is not None)
+    assert abs(top + math.log(s) - N * math.log(p["q"])) < 0.05
+    for r in runs:
+        assert TC_Q10 < r["Tc_equal_peak"] < TC_Q10 + 0.08
+        assert r["ln_suppression"] < 0
+        assert -2 * N <= r["E_peaks"][0] < r["E_peaks"][1] <= 0
+    return d
+
+
+def test_converged_oracle_values_potts10_L20():
+    """16 converged oracle runs of the q=10 L=20 workload (written by
+    tests/golden/make_converged.py): the canonical analysis of each, and the
+    per-bin mean and spread of ln g, are consistent."""
+    d = _check_converged_file("potts10_L20", range(1, 17))
+    for r in d["runs"]:
+        assert abs(r["c_peak_T"] - r["Tc_equal_peak"]) < 0.002
+
+
+def test_tc_of_L_approaches_the_exact_value_from_above():
+    """Sec. 3.1: the finite-size transition temperature lies above
+    1/ln(1 + sqrt 10), falls as L grows, and a fit Tc(L) = Tc + b/N over the
+    oracle's L = 8 ... 20 runs extrapolates to the exact value within 1e-3
+    (the paper extrapolates from L up to 300 to within 2e-6; at these sizes
+    corrections beyond 1/N remain)."""
+    series = []
+    for L, seeds in ((8, range(1, 9)), (12, range(1, 9)), (16, range(1, 9)), (20, range(1, 17))):
+        d = _check_converged_file("potts10_L%d" % L, seeds)
+        n = len(d["runs"])
+        series.append((L * L, d["mean"]["Tc_equal_peak"], d["sd"]["Tc_equal_peak"] / math.sqrt(n)))
+    for (_, t0, e0), (_, t1, e1) in zip(series, series[1:]):
+        assert t1 < t0 - 3 * math.hypot(e0, e1)     # decreasing with L, beyond the standard errors
+    assert all(t > TC_Q10 for _, t, _ in series)
+    # weighted least squares for Tc(L) = a + b / N
+    w = [1.0 / e ** 2 for _, _, e in series]
+    x = [1.0 / N for N, _, _ in series]
+    y = [t for _, t, _ in series]
+    sw = sum(w)
+    xm = sum(wi * xi for wi, xi in zip(w, x)) / sw
+    ym = sum(wi * yi for wi, yi in zip(w, y)) / sw
+    b = sum(wi * (xi - xm) * (yi - ym) for wi, xi, yi in zip(w, x, y)) / sum(wi * (xi - xm) ** 2 for wi, xi in zip(w, x))
+    a = ym - b * xm
+    assert b > 0
+    assert abs(a - TC_Q10) < 1e-3
