@@ -8,6 +8,8 @@ import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "librewl.so")
+# REWL_DEBUG=1 selects the build with the kernels' bounds checks (build.build(debug=True)).
+LIB_DEBUG_PATH = os.path.join(HERE, "_build", "librewl_debug.so")
 
 REWL_OK = 0
 STATUS_NAMES = {0: "REWL_OK", 1: "REWL_ERR_ARG", 2: "REWL_ERR_NOMEM", 3: "REWL_ERR_CUDA",
@@ -59,9 +61,10 @@ def load():
     global _lib
     if _lib is not None:
         return _lib
-    if not os.path.exists(LIB_PATH):
-        raise RuntimeError("librewl.so is not built (%s); run __graft_entry__.build() first" % LIB_PATH)
-    L = C.CDLL(LIB_PATH)
+    path = LIB_DEBUG_PATH if os.environ.get("REWL_DEBUG") == "1" else LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError("%s is not built; run __graft_entry__.build() (or build.build(debug=True)) first" % path)
+    L = C.CDLL(path)
     vp, i32, ll, sz, dbl = C.c_void_p, C.c_int, C.c_longlong, C.c_size_t, C.c_double
     H = C.c_void_p
     st = C.c_int

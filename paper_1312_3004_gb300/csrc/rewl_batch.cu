@@ -118,6 +118,8 @@ rewl_status read_batch_status(rewl_batch_s *b, int *done) {
         const rewl::Ctl &c = b->h_ctls[i];
         if (c.error & rewl::ERR_OVERFLOW) return fail(REWL_ERR_OVERFLOW, "instance %zu: a histogram bin reached 2^31", i);
         if (c.error & rewl::ERR_ENTRY) return fail(REWL_ERR_STATE, "instance %zu: a walker could not enter its window", i);
+        if (c.error & rewl::ERR_BOUNDS)
+            return fail(REWL_ERR_STATE, "instance %zu: an index failed its bounds check (debug build)", i);
         d += c.all_done ? 1 : 0;
     }
     if (done) *done = d;

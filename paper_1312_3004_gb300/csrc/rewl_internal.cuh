@@ -29,7 +29,25 @@ struct Ctl {
 enum : unsigned int {
     ERR_OVERFLOW = 1u,  // an H bin reached 2^31
     ERR_ENTRY = 2u,     // a walker could not reach its window
+    ERR_BOUNDS = 4u,    // debug build: an index failed its bounds check
 };
+
+// Bounds checks of the debug build (REWL_DEBUG_CHECKS): an index outside
+// [lo, hi) counts into `bad` and is replaced by lo, so the access stays inside
+// the array and the kernel finishes; the caller raises ERR_BOUNDS.  In the
+// release build the index passes through unchanged.
+#ifdef REWL_DEBUG_CHECKS
+__device__ __forceinline__ int checked_index(int i, int lo, int hi, unsigned int &bad) {
+    if (i < lo || i >= hi) {
+        ++bad;
+        return lo;
+    }
+    return i;
+}
+#define REWL_IDX(i, lo, hi, bad) rewl::checked_index((i), (lo), (hi), (bad))
+#else
+#define REWL_IDX(i, lo, hi, bad) (i)
+#endif
 
 // Random-number domains: the fourth Philox counter word.
 enum : uint32_t { DOM_WL = 0, DOM_INIT = 1, DOM_ENTRY = 2, DOM_PERM = 3, DOM_XACC = 4 };

@@ -193,6 +193,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(Model M, State S, int P) {
         int E = S.cfg_E[c];
         unsigned long long t = S.t[g];
         unsigned long long n_acc = 0, n_tie = 0;
+        unsigned int bad = 0;  // failed bounds checks (debug build)
         const uint32_t N = (uint32_t)M.N, qm1 = (uint32_t)(M.q - 1);
         for (long long k = 0; k < M.K; ++k, ++t) {
             const uint4 r = philox((uint32_t)t, (uint32_t)(t >> 32), (uint32_t)g, DOM_WL, M.key0, M.key1);
@@ -202,7 +203,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(Model M, State S, int P) {
             const int nw = v + (v >= cur);
             const int En = E + delta_e<BITS>(lat, neighbours(site, M.L, M.N, M.divL), cur, nw);
             if (En >= lo && En <= hi) {
-                const double d = __dsub_rn(lg[E - lo], lg[En - lo]);
+                const double d = __dsub_rn(lg[REWL_IDX(E - lo, 0, M.B, bad)], lg[REWL_IDX(En - lo, 0, M.B, bad)]);
                 bool acc = d >= 0.0;
                 if (!acc) {
                     const double u = unit53(r.z, r.w);
@@ -216,14 +217,16 @@ __global__ void __launch_bounds__(256) sweep_kernel(Model M, State S, int P) {
                     ++n_acc;
                 }
             }
-            lg[E - lo] = __dadd_rn(lg[E - lo], lnf);
-            hg[E - lo] += 1u;
+            const int b = REWL_IDX(E - lo, 0, M.B, bad);
+            lg[b] = __dadd_rn(lg[b], lnf);
+            hg[b] += 1u;
         }
         S.cfg_E[c] = E;
         S.t[g] = t;
         atomicAdd(&S.ctl->flips, (unsigned long long)M.K);
         atomicAdd(&S.ctl->accepted, n_acc);
         if (n_tie) atomicAdd(&S.ctl->ties, n_tie);
+        if (bad) atomicOr(&S.ctl->error, ERR_BOUNDS);
     }
     __syncthreads();
 

@@ -216,6 +216,9 @@ constexpr long long kForceLo = -(1LL << 62);
 struct Tally {
     unsigned long long ties, slow;
     unsigned int acc, seq;
+#ifdef REWL_DEBUG_CHECKS
+    unsigned int bad = 0;  // failed bounds checks
+#endif
 };
 
 // Binary64 bits of F * 2^(ew - 1075) for an integer F >= 0 that has at most
@@ -307,7 +310,7 @@ __device__ void walker_sweep_1(const Model &M, uint32_t *__restrict__ lat, long 
     // The current bin's shadow AF and its visits since the walker came are kept
     // in registers, and written when the walker leaves the bin.
     int Eo = E_io - lo;
-    long long AF = lgf[Eo];
+    long long AF = lgf[REWL_IDX(Eo, 0, M.B, tally.bad)];
     uint32_t visits = 0;
     unsigned int nacc = 0;
     int flipped = -1;  // site the previous step flipped
@@ -326,15 +329,15 @@ __device__ void walker_sweep_1(const Model &M, uint32_t *__restrict__ lat, long 
         const int dE = (int)(cp.sr == cp.cur) + (int)(cp.sl == cp.cur) + (int)(cp.sd == cp.cur) + (int)(cp.su == cp.cur) -
                        (int)(cp.sr == nw) - (int)(cp.sl == nw) - (int)(cp.sd == nw) - (int)(cp.su == nw);
         const int En = Eo + dE;
-        const long long BF = dE == 0 ? AF : lgf[En];  // beyond the window: kOutside
+        const long long BF = dE == 0 ? AF : lgf[REWL_IDX(En, -kPad, M.B + kPad, tally.bad)];  // beyond: kOutside
         Prop np;
         if (i + 1 < M.K) draw(t_io + (unsigned long long)i + 1ull, np);
         const long long D = BF - AF;
         bool acc = D < cp.th.x;
         if (!acc && D < cp.th.y) {  // inside the bracket (never beyond the window)
             tally.slow += 1;
-            const long long Ab = (AF & 1) ? lgb[Eo] : from_units(AF >> 1, ew);
-            const long long Bb = (BF & 1) ? lgb[En] : from_units(BF >> 1, ew);
+            const long long Ab = (AF & 1) ? lgb[REWL_IDX(Eo, 0, M.B, tally.bad)] : from_units(AF >> 1, ew);
+            const long long Bb = (BF & 1) ? lgb[REWL_IDX(En, 0, M.B, tally.bad)] : from_units(BF >> 1, ew);
             acc = dE == 0 ? true : exact_accept(Ab, Bb, cp.U, &tally.ties);
         }
         const long long cur = acc ? BF : AF;  // with dE = 0 both are the current shadow
@@ -342,9 +345,9 @@ __device__ void walker_sweep_1(const Model &M, uint32_t *__restrict__ lat, long 
         long long AF2 = cur + incF;
         if (!int_add || (cur & 1)) {  // ln g(E) += ln f in binary64
             tally.seq += 1;
-            const long long Ab = (cur & 1) ? lgb[Eb2] : from_units(cur >> 1, ew);
+            const long long Ab = (cur & 1) ? lgb[REWL_IDX(Eb2, 0, M.B, tally.bad)] : from_units(cur >> 1, ew);
             const long long A2 = exact_add(Ab, lnf);
-            lgb[Eb2] = A2;
+            lgb[REWL_IDX(Eb2, 0, M.B, tally.bad)] = A2;
             AF2 = shadow_of(A2, ew);
         } else {
             const uint32_t hc = (uint32_t)((unsigned long long)cur >> 32);
@@ -353,8 +356,8 @@ __device__ void walker_sweep_1(const Model &M, uint32_t *__restrict__ lat, long 
         }
         // (atomics whose result is not used: the walker does not wait for them)
         if (Eb2 != Eo) {  // leaving the bin: its value and visits go to memory
-            lgf[Eo] = AF;
-            atomicAdd(&hg[Eo], visits);
+            lgf[REWL_IDX(Eo, 0, M.B, tally.bad)] = AF;
+            atomicAdd(&hg[REWL_IDX(Eo, 0, M.B, tally.bad)], visits);
             visits = 0;
         }
         ++visits;
@@ -666,14 +669,14 @@ __device__ void walker_sweep(const Model &M, uint32_t *__restrict__ lat, long lo
                 kxr = (uint32_t)(kc ^ knw) << ((ks & (per - 1)) * BITS);
             }
             const int En = Eo + kdE;
-            const long long BF = lgf[En];
+            const long long BF = lgf[REWL_IDX(En, -kPad, M.B + kPad, tally.bad)];
             const long long D = BF - AF;
             bool acc = D < tlo;
             if (!acc && D < thi) {  // inside the bracket (never beyond the window)
                 tally.slow += 1;
                 const unsigned long long kU = from_lane<S>(gm, U, kk);
-                const long long Ab = (AF & 1) ? lgb[Eo] : from_units(AF >> 1, ew);
-                const long long Bb = (BF & 1) ? lgb[En] : from_units(BF >> 1, ew);
+                const long long Ab = (AF & 1) ? lgb[REWL_IDX(Eo, 0, M.B, tally.bad)] : from_units(AF >> 1, ew);
+                const long long Bb = (BF & 1) ? lgb[REWL_IDX(En, 0, M.B, tally.bad)] : from_units(BF >> 1, ew);
                 acc = kdE == 0 ? true : exact_accept(Ab, Bb, kU, &tally.ties);
             }
             const long long cur = acc ? BF : AF;
@@ -681,16 +684,16 @@ __device__ void walker_sweep(const Model &M, uint32_t *__restrict__ lat, long lo
             long long AF2 = cur + incF;
             if (!int_add || (cur & 1)) {  // ln g(E) += ln f in binary64
                 tally.seq += 1;
-                const long long Ab = (cur & 1) ? lgb[Eb2] : from_units(cur >> 1, ew);
+                const long long Ab = (cur & 1) ? lgb[REWL_IDX(Eb2, 0, M.B, tally.bad)] : from_units(cur >> 1, ew);
                 const long long A2 = exact_add(Ab, lnf);
-                lgb[Eb2] = A2;
+                lgb[REWL_IDX(Eb2, 0, M.B, tally.bad)] = A2;
                 AF2 = shadow_of(A2, ew);
             } else {
                 AF2 = round_shadow(AF2);
             }
             Eo = Eb2;
             AF = AF2;
-            lgf[Eo] = AF;
+            lgf[REWL_IDX(Eo, 0, M.B, tally.bad)] = AF;
             pcur = pbase + (uint32_t)Eo * 8u;
             if (acc) {
                 if (S == 1 || j == 0) atomicXor(&lat[kword], kxr);
@@ -713,13 +716,13 @@ __device__ void walker_sweep(const Model &M, uint32_t *__restrict__ lat, long lo
         }
         const int bin = Eb + x;
         if (S == 1) {
-            atomicAdd(&hg[bin], 1u);
+            atomicAdd(&hg[REWL_IDX(bin, 0, M.B, tally.bad)], 1u);
         } else {  // one add per run of equal bins, by the run's last step
             const int nxt = __shfl_down_sync(gm, bin, 1, S);
             const bool last = j < n && (j == n - 1 || nxt != bin);
             const unsigned ends = __ballot_sync(gm, last) >> gbase;
             const unsigned below = ends & ((1u << j) - 1u);  // j < 32
-            if (last) atomicAdd(&hg[bin], (uint32_t)(j - (below ? 31 - __clz((int)below) : -1)));
+            if (last) atomicAdd(&hg[REWL_IDX(bin, 0, M.B, tally.bad)], (uint32_t)(j - (below ? 31 - __clz((int)below) : -1)));
         }
         nacc += (uint32_t)__popc(accm);
         if (S > 1) __syncwarp(gm);
@@ -788,6 +791,9 @@ __device__ void sweep_block(const Model &M, const State &Sg, int g0, int P, cons
             if (tally.slow) atomicAdd(&Sg.ctl->slow, tally.slow);
             if (tally.ties) atomicAdd(&Sg.ctl->ties, tally.ties);
             if (tally.seq) atomicAdd(&Sg.ctl->seq, (unsigned long long)tally.seq);
+#ifdef REWL_DEBUG_CHECKS
+            if (tally.bad) atomicOr(&Sg.ctl->error, ERR_BOUNDS);
+#endif
         }
     }
     __syncthreads();
@@ -859,6 +865,9 @@ __global__ void __launch_bounds__(256) batch_walker_kernel(const InstDev *inst, 
     if (tally.slow) atomicAdd(&Sr.ctl->slow, tally.slow);
     if (tally.ties) atomicAdd(&Sr.ctl->ties, tally.ties);
     if (tally.seq) atomicAdd(&Sr.ctl->seq, (unsigned long long)tally.seq);
+#ifdef REWL_DEBUG_CHECKS
+    if (tally.bad) atomicOr(&Sr.ctl->error, ERR_BOUNDS);
+#endif
 }
 
 Layout make_layout(const Model &M, int S, bool lat_global) {

@@ -38,6 +38,23 @@ def test_library_exports_every_declared_symbol():
     assert lib.rewl_version().startswith(b"rewl-gb300")
 
 
+@pytest.mark.slow
+def test_debug_build_with_bounds_checks(monkeypatch):
+    """The build with the kernels' bounds checks compiles (sm_103a) and exports
+    the same entry points; REWL_DEBUG=1 makes the package load it."""
+    from paper_1312_3004_gb300 import build
+
+    path = build.build(debug=True)
+    assert path.endswith("librewl_debug.so") and os.path.exists(path)
+    monkeypatch.setenv("REWL_DEBUG", "1")
+    monkeypatch.setattr(_lib, "_lib", None)
+    lib = _lib.load()
+    assert lib._name == path
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert lib.rewl_server_release(None, 1) == 1   # host paths behave alike
+
+
 @pytest.mark.parametrize("args", [
     (1, 8, 4, 0.75, 2, 1e-6, 0.8, 1000, 1),       # q < 2
     (2, 2, 4, 0.75, 2, 1e-6, 0.8, 1000, 1),       # L < 3
