@@ -138,6 +138,8 @@ rewl_status read_ctl(rewl_s *h) {
     if (h->h_ctl->error & rewl::ERR_OVERFLOW) return fail(REWL_ERR_OVERFLOW, "a histogram bin reached 2^31 visits");
     if (h->h_ctl->error & rewl::ERR_ENTRY) return fail(REWL_ERR_STATE, "a walker could not enter its window");
     if (h->h_ctl->error & rewl::ERR_BOUNDS) return fail(REWL_ERR_STATE, "an index failed its bounds check (debug build)");
+    if (h->h_ctl->error & rewl::ERR_ENERGY)
+        return fail(REWL_ERR_STATE, "a walker's energy differs from its recount (debug build)");
     return REWL_OK;
 }
 

@@ -30,6 +30,7 @@ enum : unsigned int {
     ERR_OVERFLOW = 1u,  // an H bin reached 2^31
     ERR_ENTRY = 2u,     // a walker could not reach its window
     ERR_BOUNDS = 4u,    // debug build: an index failed its bounds check
+    ERR_ENERGY = 8u,    // debug build: a kept energy differs from its recount
 };
 
 // Bounds checks of the debug build (REWL_DEBUG_CHECKS): an index outside

@@ -500,6 +500,18 @@ __global__ void recount_kernel(Model M, State S) {
     S.cfg_E[c] = recount_energy<BITS>(S.spins + (size_t)c * M.wpc, M);
 }
 
+#ifdef REWL_DEBUG_CHECKS
+// Debug build, before every window check: the energy each walker keeps
+// incrementally must equal a full recount of its configuration (Eq. 2).
+template <int BITS>
+__global__ void energy_check_kernel(Model M, State S) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= M.G || S.done[g / M.m] || *(volatile unsigned int *)&S.ctl->all_done) return;
+    const uint32_t c = S.slot_cfg[g];
+    if (S.cfg_E[c] != recount_energy<BITS>(S.spins + (size_t)c * M.wpc, M)) atomicOr(&S.ctl->error, ERR_ENERGY);
+}
+#endif
+
 // ---------------------------------------------------------------------------
 size_t sweep_smem_per_walker(const Model &M) {
     return (size_t)M.B * (sizeof(double) + sizeof(uint32_t)) + (size_t)M.wpc * sizeof(uint32_t);
@@ -567,6 +579,10 @@ cudaError_t launch_sweep(const Model &M, const State &S, const SweepPlan &p, cud
 }
 
 cudaError_t launch_window_check(const Model &M, const State &S, cudaStream_t s) {
+#ifdef REWL_DEBUG_CHECKS
+    if (M.bits == 8) energy_check_kernel<8><<<(M.G + 63) / 64, 64, 0, s>>>(M, S);
+    else energy_check_kernel<4><<<(M.G + 63) / 64, 64, 0, s>>>(M, S);
+#endif
     window_check_kernel<<<M.h, CHECK_THREADS, 0, s>>>(M, S);
     return cudaGetLastError();
 }

@@ -161,6 +161,8 @@ extern "C" rewl_status rewl_run_static(const rewl_params *prm, int spin_bits, lo
         if (ctl.error & rewl::ERR_OVERFLOW) return fail_static(REWL_ERR_OVERFLOW, "a histogram bin reached 2^31");
         if (ctl.error & rewl::ERR_ENTRY) return fail_static(REWL_ERR_STATE, "a walker could not enter its window");
         if (ctl.error & rewl::ERR_BOUNDS) return fail_static(REWL_ERR_STATE, "an index failed its bounds check (debug build)");
+        if (ctl.error & rewl::ERR_ENERGY)
+            return fail_static(REWL_ERR_STATE, "a walker's energy differs from its recount (debug build)");
         return REWL_OK;
     };
 
