@@ -52,22 +52,24 @@ struct Moments {
 };
 
 // Canonical averages at T over the bins, weights g(E) exp(-E/T) scaled by the
-// largest one; the variance is taken about the mean (no cancellation).
-Moments moments(const Bins &x, int N, double T) {
+// largest one (each computed once, in `w`); the variance is taken about the
+// mean (no cancellation).
+Moments moments(const Bins &x, int N, double T, std::vector<double> &w) {
     const size_t n = x.E.size();
+    w.resize(n);
     double top = -INFINITY;
     for (size_t i = 0; i < n; ++i) top = std::fmax(top, x.lg[i] - x.E[i] / T);
     double Z = 0.0, e1 = 0.0;
     for (size_t i = 0; i < n; ++i) {
-        const double w = std::exp((x.lg[i] - x.E[i] / T) - top);
-        Z += w;
-        e1 += w * x.E[i];
+        w[i] = std::exp((x.lg[i] - x.E[i] / T) - top);
+        Z += w[i];
+        e1 += w[i] * x.E[i];
     }
     e1 /= Z;
     double var = 0.0;
     for (size_t i = 0; i < n; ++i) {
-        const double w = std::exp((x.lg[i] - x.E[i] / T) - top), d = x.E[i] - e1;
-        var += w * d * d;
+        const double d = x.E[i] - e1;
+        var += w[i] * d * d;
     }
     var /= Z;
     Moments m;
@@ -91,8 +93,9 @@ rewl_status rewl_canonical(const double *lng, size_t len, const double *T, size_
     for (size_t i = 0; i < nT; ++i)
         if (bad_temperature(T[i])) return fail(REWL_ERR_ARG, "temperature %zu is not finite and > 0", i);
     const Bins x(lng, len, N);
+    std::vector<double> w;
     for (size_t i = 0; i < nT; ++i) {
-        const Moments m = moments(x, N, T[i]);
+        const Moments m = moments(x, N, T[i], w);
         out[4 * i + 0] = m.u;
         out[4 * i + 1] = m.c;
         out[4 * i + 2] = m.f;
@@ -128,7 +131,8 @@ rewl_status rewl_specific_heat_peak(const double *lng, size_t len, double T_lo, 
     if (bad_temperature(T_lo) || !std::isfinite(T_hi) || !(T_hi > T_lo))
         return fail(REWL_ERR_ARG, "temperature range [%g, %g] invalid", T_lo, T_hi);
     const Bins x(lng, len, N);
-    auto c_at = [&](double T) { return moments(x, N, T).c; };
+    std::vector<double> w;
+    auto c_at = [&](double T) { return moments(x, N, T, w).c; };
     // Scan, then golden-section search between the best point's neighbours.
     const int grid = 1024;
     const double step = (T_hi - T_lo) / grid;
