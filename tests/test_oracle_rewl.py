@@ -443,3 +443,26 @@ def test_every_walker_holds_every_replica_over_a_run():
     one = O.OracleREWL(3, 6, 1, 0.75, 3, 1e-3, 0.8, 1000, 2)
     one.run(0)
     assert np.array_equal(one.rep(), np.arange(3))
+
+
+def test_error_follows_the_square_root_of_ln_f_final():
+    """Sec. 2: the accuracy goes as sqrt(ln f_final) (read as in Zhou & Bhatt).
+    With the halving schedule this holds until the error meets its floor
+    (about 0.1 on this lattice, reached near ln f_final = 1e-4; see the 1/t
+    tests): from 1e-2 to 1e-4 the median worst-bin error against the exact
+    ln g falls by about sqrt(100) = 10."""
+    q, L, h, m, K = 3, 4, 3, 2, 1000
+    N = L * L
+    ex = O.exact_lng(O.exact_counts_tm(q, L))
+    ex = ex - (np.logaddexp.reduce(ex[np.isfinite(ex)]) - N * np.log(q))
+    fin = np.isfinite(ex)
+    med = {}
+    for lff in (1e-2, 1e-4):
+        e = []
+        for seed in range(1, 13):
+            o = O.OracleREWL(q, L, h, 0.75, m, lff, 0.8, K, seed)
+            assert o.run(20000)
+            lng = o.lng_joined()
+            e.append(np.max(np.abs(lng[fin] - ex[fin])))
+        med[lff] = np.median(e)
+    assert 5.0 < med[1e-2] / med[1e-4] < 20.0
