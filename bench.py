@@ -553,7 +553,7 @@ def oracle_reference(workload, seed, analysis, lng=None):
                                  abs(analysis["c_peak"] - r["c_peak"]) <= 1e-9 * r["c_peak"] and
                                  analysis.get("E_peaks") == r["E_peaks"])
     for key in ("c_peak_T", "c_peak", "Tc_equal_peak"):
-        if analysis.get(key) is not None and ref["sd"][key] > 0:
+        if analysis.get(key) is not None and ref["sd"].get(key) and ref["mean"].get(key) is not None:
             out.setdefault("sigmas_from_oracle_mean", {})[key] = (analysis[key] - ref["mean"][key]) / ref["sd"][key]
     if lng is not None and "lng_mean" in ref:
         # the run's normalised ln g against the oracle's seed mean, bin by bin, in

@@ -1,5 +1,5 @@
 """Writes tests/golden/<workload>_converged.json: the oracle's converged runs
-of a named 10-state Potts workload (paper_1312_3004_gb300/workloads.py) for a
+of a named Potts workload (paper_1312_3004_gb300/workloads.py) for a
 range of seeds, and the canonical analysis of each joined ln g (Sec. 3.1): the
 specific-heat maximum, the equal-peak temperature Tc(L) and the suppression of
 the transition states, searched within [0.8, 1.3] x 1/ln(1 + sqrt q); with the
@@ -45,10 +45,12 @@ def one(job):
     tc_inf = 1.0 / math.log(1.0 + math.sqrt(p["q"]))
     lo, hi = 0.8 * tc_inf, 1.3 * tc_inf
     T, c = TH.specific_heat_peak(lng, lo, hi)
-    Tc, e_low, e_high, ln_sup = TH.equal_peak_temperature(lng, lo, hi)
+    peaks = TH.equal_peak_temperature(lng, lo, hi)   # None: no double peak (q = 2)
+    Tc, e_low, e_high, ln_sup = peaks if peaks is not None else (None, None, None, None)
     steps = int(o.t().sum())
     return {"lng": [float(x) for x in lng], "seed": seed, "rounds": int(o.round), "wl_steps": steps, "oracle_seconds": round(secs, 1),
-            "c_peak_T": T, "c_peak": c, "Tc_equal_peak": Tc, "E_peaks": [e_low, e_high],
+            "c_peak_T": T, "c_peak": c, "Tc_equal_peak": Tc,
+            "E_peaks": [e_low, e_high] if e_low is not None else None,
             "ln_suppression": ln_sup}
 
 
@@ -92,7 +94,11 @@ def main():
     out["lng_mean"] = mean_b
     out["lng_sd"] = sd_b
     for key in ("c_peak_T", "c_peak", "Tc_equal_peak", "ln_suppression"):
-        v = [r[key] for r in runs]
+        v = [r[key] for r in runs if r[key] is not None]
+        if len(v) < len(runs):
+            out.setdefault("mean", {})[key] = None
+            out.setdefault("sd", {})[key] = None
+            continue
         mean = sum(v) / len(v)
         sd = math.sqrt(sum((x - mean) ** 2 for x in v) / (len(v) - 1)) if len(v) > 1 else 0.0
         out.setdefault("mean", {})[key] = mean

@@ -127,3 +127,29 @@ def test_tc_of_L_approaches_the_exact_value_from_above():
     a = ym - b * xm
     assert b > 0
     assert abs(a - TC_Q10) < 1e-3
+
+
+def test_single_runs_lie_within_3_sigma_of_the_16_seed_mean_ising_L8():
+    """The q=2 L=8 workload: 16 converged oracle runs give the per-bin mean and
+    spread of ln g (tests/golden/ising_L8_converged.json); runs of other seeds
+    fall within 3 sigma of that mean in nearly every bin, and the mean
+    specific-heat peak lies within 3 standard errors of the exact torus's."""
+    import numpy as np
+    from oracle import thermo as TH
+
+    d = load("ising_L8_converged.json")
+    assert [r["seed"] for r in d["runs"]] == list(range(1, 17))
+    mean = np.array([np.nan if m is None else m for m in d["lng_mean"]])
+    sd = np.array([np.nan if v is None else v for v in d["lng_sd"]])
+    ok = np.isfinite(mean)
+    exact = O.exact_lng(O.exact_counts_tm(2, 8))
+    assert np.array_equal(ok, np.isfinite(exact))          # the support: even k except 2 and 126
+    p = WL.params("ising_L8")
+    for seed in (17, 18, 19, 20):
+        o = O.OracleREWL(*WL.rewl_args(p, seed))
+        assert o.run(0)
+        z = (o.lng_joined()[ok] - mean[ok]) / sd[ok]
+        assert np.mean(np.abs(z) <= 3.0) >= 0.9 and np.max(np.abs(z)) < 6.0, seed
+    T_x, c_x = TH.specific_heat_peak(exact, 0.8, 2.0)
+    se = d["sd"]["c_peak_T"] / 4.0
+    assert abs(d["mean"]["c_peak_T"] - T_x) < 3 * se
