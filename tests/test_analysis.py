@@ -195,3 +195,19 @@ def test_ising_energy_equals_the_spin_sum_on_every_configuration():
     for bad in ((8, -1), (8, 129), (2, 0)):
         with pytest.raises(P.RewlError):
             P.ising_energy(*bad)
+
+
+def test_join_without_a_common_bin_is_a_state_error():
+    """Two windows whose visited bins do not overlap cannot be joined (Fig. 2
+    needs a bin where both slopes exist): the library and the oracle refuse."""
+    _lib_or_skip()
+    e_lo, W = O.window_table(4, 2, 0.75)
+    lw = np.zeros((2, W + 1))
+    mw = np.zeros((2, W + 1), dtype=np.uint8)
+    mw[0, :3] = 1      # the lower window visited only its first bins
+    mw[1, -3:] = 1     # the upper window only its last ones
+    with pytest.raises(P.RewlError) as err:
+        P.join(2, 4, e_lo, W, lw, mw)
+    assert err.value.status == 6
+    with pytest.raises(RuntimeError):
+        O.join_pieces(16, e_lo, W, lw, mw)
