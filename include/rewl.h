@@ -245,18 +245,28 @@ rewl_status rewl_get_stats(rewl_t h, rewl_stats *stats);
  *                                      2 window h-1
  *   REWL_FIELD_PHASE  uint8  [h]       1/t rule (REWL_OPT_SCHEDULE = 1): 1 once window i
  *                                      follows ln f = 1/t, else 0
+ *   REWL_FIELD_TIES   uint64 [32][2]   the first 32 near-tie acceptance draws
+ *                                      (|u - exp(D)| < 1e-14, where the exp of two
+ *                                      libraries may decide differently; all of
+ *                                      them are counted in rewl_stats.near_ties):
+ *                                      entry i = (kind << 32 | who, when); kind 0 a
+ *                                      WL step of walker slot `who` at its step
+ *                                      index `when`; kind 1 an exchange of the pair
+ *                                      whose lower-window walker is slot `who`, in
+ *                                      round `when`; entries at or beyond
+ *                                      near_ties are zero (read-only)
  * bytes must equal the size above, else REWL_ERR_ARG. */
 enum {
     REWL_FIELD_SPINS = 0, REWL_FIELD_ENERGY = 1, REWL_FIELD_REPLICA = 2, REWL_FIELD_STEPS = 3,
     REWL_FIELD_LNG = 4, REWL_FIELD_HIST = 5, REWL_FIELD_MASK = 6, REWL_FIELD_LNF = 7,
     REWL_FIELD_ITER = 8, REWL_FIELD_DONE = 9, REWL_FIELD_ELO = 10, REWL_FIELD_ROUND = 11,
-    REWL_FIELD_TRIPS = 12, REWL_FIELD_TRIP_END = 13, REWL_FIELD_PHASE = 14
+    REWL_FIELD_TRIPS = 12, REWL_FIELD_TRIP_END = 13, REWL_FIELD_PHASE = 14, REWL_FIELD_TIES = 15
 };
 rewl_status rewl_get_field(rewl_t h, int field, void *out, size_t bytes);
 
 /* Overwrite one state array from host memory (same layouts as rewl_get_field;
- * REWL_FIELD_SPINS also recounts the energies; REWL_FIELD_ELO and
- * REWL_FIELD_REPLICA are read-only).  For tests that start from a chosen
+ * REWL_FIELD_SPINS also recounts the energies; REWL_FIELD_ELO,
+ * REWL_FIELD_REPLICA, REWL_FIELD_ENERGY and REWL_FIELD_TIES are read-only).  For tests that start from a chosen
  * state, e.g. fixed weights with ln f = 0. */
 rewl_status rewl_set_field(rewl_t h, int field, const void *in, size_t bytes);
 
@@ -387,9 +397,9 @@ void rewl_server_destroy(rewl_server_t s);
  * *converged (host, may be NULL) is 1 when every window finished.  Work is
  * queued on `stream` (cudaStream_t as void*, NULL = default stream) and the
  * call synchronises it before returning.
- * The first call on a device looks up the array's device address (with that
- * device current) and caches it; make that first call before any stream
- * capture.  The array is shared by every call: each call clears what must
+ * The first call on a device (and the first after that device's context was
+ * reset) looks up the array's device address, with that device current, and
+ * caches it for that context; make that first call before any stream capture.  The array is shared by every call: each call clears what must
  * start at zero, and calls whose work overlaps on the GPU race on it.
  * Errors: REWL_ERR_ARG (parameters, NULL lng_out, wrong out_bins, or an
  * instance whose state exceeds the 16 MiB array), REWL_ERR_CUDA,

@@ -80,6 +80,10 @@ def lib():
         L.orc_obin.restype = i32
         L.orc_walker_visited_all.argtypes = [vp, i32]
         L.orc_walker_visited_all.restype = i32
+        L.orc_invert_decision.argtypes = [vp, i32, u64, u64]
+        L.orc_invert_decision.restype = i32
+        L.orc_get_ties.argtypes = [vp, vp, vp, i32]
+        L.orc_get_ties.restype = i64
         L.ex_brute_force.argtypes = [i32, i32, vp]
         L.ex_brute_force.restype = i32
         L.ex_transfer_matrix.argtypes = [i32, i32, i32, vp, vp]
@@ -210,6 +214,24 @@ class OracleREWL:
     def rt_end(self): return self._get("orc_get_rt_end", self.G, np.uint8)
     def rt_trips(self): return self._get("orc_get_rt_trips", self.G, np.uint32)
     def phase(self): return self._get("orc_get_phase", self.h, np.uint8)
+
+    # Decisions are named (kind, who, when): kind 0 a WL step of walker `who` at
+    # its step index `when`; kind 1 the exchange of the pair whose lower-window
+    # walker is `who`, in round `when`.
+    def invert_decision(self, kind, who, when):
+        """Invert one acceptance decision when it comes up (test support: to
+        reproduce what another implementation decided at a near tie)."""
+        if lib().orc_invert_decision(self._h, kind, who, when):
+            raise ValueError("too many inverted decisions")
+
+    def ties(self):
+        """(count, [(kind, who, when, |u - exp(D)|), ...]) of the draws with
+        |u - exp(D)| < 1e-12 so far (the first 64 are listed)."""
+        ent = np.zeros((64, 3), dtype=np.uint64)
+        gap = np.zeros(64)
+        n = int(lib().orc_get_ties(self._h, _ptr(ent), _ptr(gap), 64))
+        k = min(n, 64)
+        return n, [(int(a), int(b), int(c), float(d)) for (a, b, c), d in zip(ent[:k], gap[:k])]
 
     def set_schedule(self, schedule):
         """0: ln f halves per iteration (Sec. 2); 1: the 1/t rule."""

@@ -106,11 +106,24 @@ static double orc_u53(uint32_t hi, uint32_t lo)
     return (double)bits * 0x1p-53;
 }
 
-/* Metropolis-type acceptance with ratio exp(d): min[1, exp(d)] (Sec. 2). */
-static int orc_accept(double d, double u)
-{
-    return d >= 0.0 || u < exp(d);
-}
+/* Decision bookkeeping for the GPU comparison (test support, no effect on a
+ * run unless a test asks for it).  A draw with |u - exp(d)| below
+ * ORC_TIE_NEAR is logged: two libraries' exp can decide such a draw
+ * differently.  A test can also ask for given decisions to be inverted, to
+ * reproduce what another implementation did at a near tie.  Decisions are
+ * named by (kind, who, when): kind 0 a WL step of walker `who` at its step
+ * index `when`; kind 1 the exchange of the pair whose lower-window walker is
+ * `who`, in round `when`. */
+#define ORC_TIE_NEAR 1e-12
+#define ORC_TIE_LOG 64
+#define ORC_MAX_INVERT 16
+typedef struct orc_decisions {
+    int n_invert;
+    uint64_t invert[ORC_MAX_INVERT][3];
+    int64_t n_ties;                      /* near-tie draws seen (all of them)   */
+    uint64_t tie[ORC_TIE_LOG][3];        /* first ORC_TIE_LOG: kind, who, when */
+    double tie_gap[ORC_TIE_LOG];         /* |u - exp(d)| of each               */
+} orc_decisions;
 
 /* ------------------------------------------------------------------------- */
 /* Energy windows (Sec. 2, Fig. 1; geometry pinned by the L=300 run of Sec. 3.1:
@@ -200,9 +213,60 @@ typedef struct orc_rewl {
     int64_t round;   /* barriers (exchange rounds) completed                  */
     uint64_t xtried, xacc;
     int status;
+    orc_decisions dec; /* near-tie log and inverted decisions (test support) */
 } orc_rewl;
 
 enum { ORC_OK = 0, ORC_ERR_ARG = 1, ORC_ERR_NOMEM = 2, ORC_ERR_OVERFLOW = 5, ORC_ERR_STATE = 6 };
+
+/* Metropolis-type acceptance with ratio exp(d), i.e. min[1, exp(d)] (Sec. 2;
+ * Eq. 1 for an exchange): accept iff d >= 0 or u < exp(d); plus the
+ * bookkeeping above. */
+static int orc_decide(orc_rewl *s, int kind, uint64_t who, uint64_t when, double d, double u)
+{
+    int acc = 1;
+    if (d < 0.0) {
+        double e = exp(d);
+        double gap = fabs(u - e);
+        acc = u < e;
+        if (gap < ORC_TIE_NEAR) {
+            if (s->dec.n_ties < ORC_TIE_LOG) {
+                uint64_t *ent = s->dec.tie[s->dec.n_ties];
+                ent[0] = (uint64_t)kind; ent[1] = who; ent[2] = when;
+                s->dec.tie_gap[s->dec.n_ties] = gap;
+            }
+            s->dec.n_ties += 1;
+        }
+    }
+    for (int i = 0; i < s->dec.n_invert; ++i) {
+        const uint64_t *e = s->dec.invert[i];
+        if (e[0] == (uint64_t)kind && e[1] == who && e[2] == when) acc = !acc;
+    }
+    return acc;
+}
+
+int orc_invert_decision(orc_rewl *s, int kind, uint64_t who, uint64_t when)
+{
+    if (s->dec.n_invert >= ORC_MAX_INVERT) return ORC_ERR_ARG;
+    uint64_t *e = s->dec.invert[s->dec.n_invert++];
+    e[0] = (uint64_t)kind; e[1] = who; e[2] = when;
+    return ORC_OK;
+}
+
+/* Near-tie log: returns the number of near ties seen; fills up to `cap`
+ * entries (kind, who, when) and their gaps |u - exp(d)|. */
+int64_t orc_get_ties(const orc_rewl *s, uint64_t *entries, double *gaps, int cap)
+{
+    int n = s->dec.n_ties < ORC_TIE_LOG ? (int)s->dec.n_ties : ORC_TIE_LOG;
+    if (n > cap) n = cap;
+    for (int i = 0; i < n; ++i) {
+        entries[3 * i] = s->dec.tie[i][0];
+        entries[3 * i + 1] = s->dec.tie[i][1];
+        entries[3 * i + 2] = s->dec.tie[i][2];
+        gaps[i] = s->dec.tie_gap[i];
+    }
+    return s->dec.n_ties;
+}
+
 
 void orc_destroy(orc_rewl *s)
 {
@@ -369,7 +433,7 @@ void orc_wl_steps(orc_rewl *s, int g, int64_t n)
         int32_t En = E + orc_delta_e(L, sg, site, cur, nw);
         if (En >= lo && En <= hi) {
             double d = lg[E - lo] - lg[En - lo];
-            if (orc_accept(d, orc_u53(r[2], r[3]))) {
+            if (orc_decide(s, 0, (uint64_t)g, t, d, orc_u53(r[2], r[3]))) {
                 sg[site] = (uint8_t)nw;
                 E = En;
             }
@@ -556,7 +620,7 @@ void orc_exchange(orc_rewl *s)
             double d = (li[Ei - lo_a] - li[Ej - lo_a]) + (lj[Ej - lo_b] - lj[Ei - lo_b]);
             orc_draw(s->seed, rnd, (uint32_t)k, (uint32_t)a, ORC_DOM_XACC, r);
             s->xtried += 1;
-            if (!orc_accept(d, orc_u53(r[0], r[1]))) continue;
+            if (!orc_decide(s, 1, (uint64_t)gi, (uint64_t)s->round, d, orc_u53(r[0], r[1]))) continue;
             s->xacc += 1;
             memcpy(tmp, s->sigma + (size_t)gi * N, (size_t)N);
             memcpy(s->sigma + (size_t)gi * N, s->sigma + (size_t)gj * N, (size_t)N);

@@ -21,7 +21,7 @@ PHASE_SWEEP, PHASE_CHECK, PHASE_EXCHANGE = 0, 1, 2
 OPT_SWEEP_KERNEL, OPT_LANES, OPT_WALKERS_PER_CTA, OPT_LATTICE, OPT_STALL_MS, OPT_SCHEDULE = 0, 1, 2, 3, 4, 5
 SCHEDULE_HALVING, SCHEDULE_INV_T = 0, 1
 FIELD_MASK, FIELD_LNF, FIELD_ITER, FIELD_DONE, FIELD_ELO, FIELD_ROUND = 6, 7, 8, 9, 10, 11
-FIELD_TRIPS, FIELD_TRIP_END, FIELD_PHASE = 12, 13, 14
+FIELD_TRIPS, FIELD_TRIP_END, FIELD_PHASE, FIELD_TIES = 12, 13, 14, 15
 
 
 class RewlError(RuntimeError):

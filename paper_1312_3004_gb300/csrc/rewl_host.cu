@@ -326,7 +326,8 @@ rewl_status prepare_instance(rewl_s *h, const rewl_params &p, int spin_bits, int
                     rewl::fast_smem_per_walker(M, h->plan.lanes, h->plan.lat_global != 0), h->smem_optin);
     const size_t G = (size_t)M.G, B = (size_t)M.B, hh = (size_t)M.h;
     const size_t sizes[] = {G * M.wpc * 4, G * 4, G * 4, G * 8, G * B * 8, G * B * 4, hh * B, hh * 4, hh * 8, hh * 4, hh,
-                            G, G * 4, G * (B + 2 * rewl::kShadowPad) * 8, hh, sizeof(Ctl)};
+                            G, G * 4, G * (B + 2 * rewl::kShadowPad) * 8, hh, (size_t)rewl::kTieLog * 16,
+                            sizeof(Ctl)};
     size_t off = 0;
     h->parts.clear();
     for (size_t sz : sizes) {
@@ -356,7 +357,8 @@ void carve_instance(rewl_s *h, void *base) {
     S.rt_trips = (uint32_t *)at(12);
     S.shadow = (long long *)at(13);
     S.phase = (uint8_t *)at(14);
-    S.ctl = (Ctl *)at(15);  // last: save / load treat the last part as the control block
+    S.tlog = (unsigned long long *)at(15);
+    S.ctl = (Ctl *)at(16);  // last: save / load treat the last part as the control block
 }
 
 cudaError_t init_instance_async(rewl_s *h, cudaStream_t s) {
@@ -686,6 +688,7 @@ static rewl_status field_geometry(rewl_t h, int field, void **dev, size_t *bytes
     case REWL_FIELD_TRIPS: *dev = h->S.rt_trips; *bytes = G * 4; break;
     case REWL_FIELD_TRIP_END: *dev = h->S.rt_end; *bytes = G; break;
     case REWL_FIELD_PHASE: *dev = h->S.phase; *bytes = hh; break;
+    case REWL_FIELD_TIES: *dev = h->S.tlog; *bytes = (size_t)rewl::kTieLog * 16; break;
     default: return fail(REWL_ERR_ARG, "unknown field %d", field);
     }
     return REWL_OK;
@@ -726,7 +729,8 @@ rewl_status rewl_get_field(rewl_t h, int field, void *out, size_t bytes) {
 rewl_status rewl_set_field(rewl_t h, int field, const void *in, size_t bytes) {
     REWL_API_TRY
     if (!h || !in) return fail(REWL_ERR_ARG, "NULL argument");
-    if (field == REWL_FIELD_ELO || field == REWL_FIELD_REPLICA || field == REWL_FIELD_ENERGY)
+    if (field == REWL_FIELD_ELO || field == REWL_FIELD_REPLICA || field == REWL_FIELD_ENERGY ||
+        field == REWL_FIELD_TIES)
         return fail(REWL_ERR_ARG, "field %d is read-only", field);
     void *dev;
     size_t need;

@@ -87,8 +87,26 @@ struct State {
     long long *shadow;    // [G][B + 2 kShadowPad] ln g shadows of the one-lane sweep that keeps
                           // every walker's state in global memory
     uint8_t *phase;       // [h] 1/t rule: 1 once the window follows ln f = 1/t
+    unsigned long long *tlog;  // [kTieLog][2] the first near-tie decisions: (kind << 32 | who, when)
     Ctl *ctl;             // control block
 };
+
+// Near-tie log.  An acceptance draw with |u - exp(D)| < 1e-14 is one where the
+// exp of two libraries can decide differently; each is counted in Ctl::ties and
+// the first kTieLog are recorded, so that a GPU / CPU difference can be traced
+// to the decision that caused it.  Kinds: a WL step (who = walker slot g, when
+// = its step index t) or an exchange (who = slot of the lower window's walker,
+// when = the exchange round).
+constexpr int kTieLog = 32;
+enum : unsigned int { TIE_WL = 0u, TIE_EXCHANGE = 1u };
+__device__ __forceinline__ void record_tie(Ctl *ctl, unsigned long long *tlog, unsigned int kind, unsigned int who,
+                                           unsigned long long when) {
+    const unsigned long long i = atomicAdd(&ctl->ties, 1ull);
+    if (i < (unsigned long long)kTieLog) {
+        tlog[2 * i] = ((unsigned long long)kind << 32) | who;
+        tlog[2 * i + 1] = when;
+    }
+}
 
 enum : int { SWEEP_REFERENCE = 0, SWEEP_FAST = 1 };
 

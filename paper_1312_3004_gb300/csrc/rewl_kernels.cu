@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(Model M, State S, int P) {
         const uint32_t c = S.slot_cfg[g];
         int E = S.cfg_E[c];
         unsigned long long t = S.t[g];
-        unsigned long long n_acc = 0, n_tie = 0;
+        unsigned long long n_acc = 0;
         unsigned int bad = 0;  // failed bounds checks (debug build)
         const uint32_t N = (uint32_t)M.N, qm1 = (uint32_t)(M.q - 1);
         for (long long k = 0; k < M.K; ++k, ++t) {
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(Model M, State S, int P) {
                     const double u = unit53(r.z, r.w);
                     const double e = exp(d);
                     acc = u < e;
-                    if (fabs(u - e) < 1e-14) ++n_tie;
+                    if (fabs(u - e) < 1e-14) record_tie(S.ctl, S.tlog, TIE_WL, (unsigned int)g, t);
                 }
                 if (acc) {
                     spin_set<BITS>(lat, site, nw);
@@ -225,7 +225,6 @@ __global__ void __launch_bounds__(256) sweep_kernel(Model M, State S, int P) {
         S.t[g] = t;
         atomicAdd(&S.ctl->flips, (unsigned long long)M.K);
         atomicAdd(&S.ctl->accepted, n_acc);
-        if (n_tie) atomicAdd(&S.ctl->ties, n_tie);
         if (bad) atomicOr(&S.ctl->error, ERR_BOUNDS);
     }
     __syncthreads();
@@ -416,7 +415,11 @@ __device__ void exchange_block(const Model &M, const State &S) {
             const uint4 r = philox((uint32_t)round, (uint32_t)k, (uint32_t)a, DOM_XACC, M.key0, M.key1);
             ++tried;
             bool ok = d >= 0.0;
-            if (!ok) ok = unit53(r.x, r.y) < exp(d);
+            if (!ok) {
+                const double u = unit53(r.x, r.y), e = exp(d);
+                ok = u < e;
+                if (fabs(u - e) < 1e-14) record_tie(ctl, S.tlog, TIE_EXCHANGE, (unsigned int)gi, round);
+            }
             if (ok) {
                 S.slot_cfg[gi] = cj;
                 S.slot_cfg[gj] = ci;

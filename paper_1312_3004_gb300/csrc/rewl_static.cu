@@ -14,12 +14,14 @@
 // on a device shares it: the state of the previous call stays in it, so each
 // call clears what must start at zero, and calls whose work overlaps on the
 // GPU (two host threads, or two streams) race on it.
-#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <mutex>
 
+#include <cuda.h>
+
 #include "rewl.h"
+#include "rewl_host_internal.hpp"
 #include "rewl_internal.cuh"
 
 namespace {
@@ -29,50 +31,61 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_rewl_static_scratch[kStaticScratchBytes];
 
+// Where the array lives on each device, and in which context that address was
+// looked up: a context torn down (cudaDeviceReset, the primary context released)
+// unloads the module, and the next context maps the array somewhere else.
+struct ScratchAddr {
+    void *ctx = nullptr;
+    unsigned char *addr = nullptr;
+};
 std::mutex g_setup_mu;
-unsigned char *g_scratch_addr[kMaxDevices] = {};
+ScratchAddr g_scratch[kMaxDevices];
 
-rewl_status fail_static(rewl_status st, const char *fmt, ...) {
-    char buf[512];
-    va_list ap;
-    va_start(ap, fmt);
-    vsnprintf(buf, sizeof buf, fmt, ap);
-    va_end(ap);
-    rewl::set_error(buf);
-    return st;
-}
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
 
-// The device address of the array.  In host code the symbol name is only a
-// host-side stand-in, so the address is looked up once per device, with that
-// device current, and cached.
-rewl_status scratch_on_current_device(unsigned char **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return fail_static(REWL_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
-    if (dev < 0 || dev >= kMaxDevices) return fail_static(REWL_ERR_ARG, "device %d out of range", dev);
-    std::lock_guard<std::mutex> lock(g_setup_mu);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_rewl_static_scratch);
-        if (e != cudaSuccess)
-            return fail_static(REWL_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-        g_scratch_addr[dev] = (unsigned char *)p;
+// The driver's cuCtxGetCurrent, reached through the runtime (no link to libcuda).
+rewl_status current_context(void **ctx) {
+    if (!g_ctx_get_current) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+            return rewl::host::fail(REWL_ERR_CUDA, "cuCtxGetCurrent not available: %s", cudaGetErrorString(e));
+        g_ctx_get_current = (CtxGetCurrentFn)fn;
     }
-    *out = g_scratch_addr[dev];
+    CUcontext c = nullptr;
+    if (g_ctx_get_current(&c) != CUDA_SUCCESS) return rewl::host::fail(REWL_ERR_CUDA, "cuCtxGetCurrent failed");
+    *ctx = (void *)c;
     return REWL_OK;
 }
 
-size_t round256(size_t x) { return (x + 255) & ~size_t(255); }
-
-// Window start energies and ln f = 1 for every window, written on the device so
-// that the host needs no buffer of its own.
-__global__ void static_setup_kernel(int32_t *e_lo, double *lnf, int h, int N, int W) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= h) return;
-    const long long R = 2LL * N;
-    const long long off = h > 1 ? (2LL * i * (R - W) + (h - 1)) / (2LL * (h - 1)) : 0LL;
-    e_lo[i] = (int32_t)(-2LL * N + off);
-    lnf[i] = 1.0;
+// The device address of the array.  In host code the symbol name is only a
+// host-side stand-in, so the address is looked up with the device current
+// (cudaGetSymbolAddress, which also creates the context) and cached per
+// device; a cached address is used only in the context it was looked up in.
+rewl_status scratch_on_current_device(unsigned char **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return rewl::host::fail(REWL_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return rewl::host::fail(REWL_ERR_ARG, "device %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_setup_mu);
+    void *ctx = nullptr;
+    rewl_status st = current_context(&ctx);
+    if (st) return st;
+    ScratchAddr &a = g_scratch[dev];
+    if (!a.addr || !ctx || a.ctx != ctx) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_rewl_static_scratch);
+        if (e != cudaSuccess)
+            return rewl::host::fail(REWL_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        st = current_context(&ctx);  // the lookup made the context current if there was none
+        if (st) return st;
+        a.ctx = ctx;
+        a.addr = (unsigned char *)p;
+    }
+    *out = a.addr;
+    return REWL_OK;
 }
 
 }  // namespace
@@ -80,101 +93,50 @@ __global__ void static_setup_kernel(int32_t *e_lo, double *lnf, int h, int N, in
 extern "C" rewl_status rewl_run_static(const rewl_params *prm, int spin_bits, long long max_rounds,
                                        double *lng_out, unsigned char *mask_out, size_t out_bins,
                                        int *converged, void *stream) {
-    if (!prm || !lng_out) return fail_static(REWL_ERR_ARG, "NULL argument");
-    const rewl_params &p = *prm;
-    if (p.q < 2 || p.q > 255 || p.L < 3 || p.L > 1024 || p.h < 1 || p.m < 1 || p.m > 256 ||
-        !(p.overlap >= 0.0 && p.overlap < 1.0) || !(p.lnf_final > 0.0 && p.lnf_final < 1.0) ||
-        !(p.flatness > 0.0 && p.flatness < 1.0) || p.exchange_interval < 1 ||
-        (spin_bits != 0 && spin_bits != 4 && spin_bits != 8) || (spin_bits == 4 && p.q > 16))
-        return fail_static(REWL_ERR_ARG, "parameter out of range");
-    const long long N = (long long)p.L * p.L, R = 2 * N;
-    long long W = (long long)std::ceil((double)R / (1.0 + (double)(p.h - 1) * (1.0 - p.overlap)));
-    if (W > R) W = R;
-    if (W < 8) return fail_static(REWL_ERR_ARG, "window width below 8 bins");
-
-    rewl::Model M{};
-    M.q = p.q;
-    M.L = p.L;
-    M.N = (int)N;
-    M.W = (int)W;
-    M.B = (int)W + 1;
-    M.h = p.h;
-    M.m = p.m;
-    M.G = p.h * p.m;
-    M.bits = spin_bits ? spin_bits : (p.q <= 16 ? 4 : 8);
-    M.wpc = (M.N * M.bits + 31) / 32;
-    M.key0 = (uint32_t)(p.seed & 0xffffffffull);
-    M.key1 = (uint32_t)(p.seed >> 32);
-    M.divL = (uint32_t)((0x100000000ull + (unsigned long long)p.L - 1) / (unsigned long long)p.L);
-    M.K = p.exchange_interval;
-    M.lnf_final = p.lnf_final;
-    M.flatness = p.flatness;
-    const size_t G = (size_t)M.G, B = (size_t)M.B, hh = (size_t)M.h;
-    if (out_bins != hh * B) return fail_static(REWL_ERR_ARG, "out_bins %zu != h * (W + 1) = %zu", out_bins, hh * B);
-
-    const size_t sizes[16] = {G * M.wpc * 4, G * 4, G * 4, G * 8, G * B * 8, G * B * 4,
-                              hh * B, hh * 4, hh * 8, hh * 4, hh, G, G * 4, G * (B + 2 * rewl::kShadowPad) * 8,
-                              hh, sizeof(rewl::Ctl)};
-    size_t offs[16], total = 0;
-    for (int i = 0; i < 16; ++i) {
-        offs[i] = total;
-        total += round256(sizes[i]);
-    }
-    if (total > kStaticScratchBytes)
-        return fail_static(REWL_ERR_ARG, "instance needs %zu bytes of state; the static scratch holds %zu", total,
-                           kStaticScratchBytes);
+    REWL_API_TRY
+    if (!prm || !lng_out) return rewl::host::fail(REWL_ERR_ARG, "NULL argument");
+    // The same checks, window table, model, sweep plan and array layout as
+    // rewl_create_ext, so that a static run and an allocating run are one run.
+    rewl_s inst;
+    rewl_s *h = &inst;
+    rewl_status st = rewl::host::prepare_instance(h, *prm, spin_bits, 0);
+    if (st) return st;
+    const rewl::Model &M = h->M;
+    const size_t B = (size_t)M.B, hh = (size_t)M.h;
+    if (out_bins != hh * B)
+        return rewl::host::fail(REWL_ERR_ARG, "out_bins %zu != h * (W + 1) = %zu", out_bins, hh * B);
+    if (h->dbytes > kStaticScratchBytes)
+        return rewl::host::fail(REWL_ERR_ARG, "instance needs %zu bytes of state; the static scratch holds %zu",
+                                h->dbytes, kStaticScratchBytes);
 
     unsigned char *base = nullptr;
-    rewl_status st = scratch_on_current_device(&base);
+    st = scratch_on_current_device(&base);
     if (st) return st;
-    int dev = 0, sms = 0, optin = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-
-    rewl::State S{};
-    S.spins = (uint32_t *)(base + offs[0]);
-    S.cfg_E = (int32_t *)(base + offs[1]);
-    S.slot_cfg = (uint32_t *)(base + offs[2]);
-    S.t = (unsigned long long *)(base + offs[3]);
-    S.lng = (double *)(base + offs[4]);
-    S.H = (uint32_t *)(base + offs[5]);
-    S.mask = (uint8_t *)(base + offs[6]);
-    S.e_lo = (int32_t *)(base + offs[7]);
-    S.lnf = (double *)(base + offs[8]);
-    S.iter = (int32_t *)(base + offs[9]);
-    S.done = (uint8_t *)(base + offs[10]);
-    S.rt_end = (uint8_t *)(base + offs[11]);
-    S.rt_trips = (uint32_t *)(base + offs[12]);
-    S.shadow = (long long *)(base + offs[13]);
-    S.phase = (uint8_t *)(base + offs[14]);
-    S.ctl = (rewl::Ctl *)(base + offs[15]);
+    rewl::host::carve_instance(h, base);
+    const rewl::State &S = h->S;
+    const rewl::SweepPlan &plan = h->plan;
 
     cudaStream_t s = (cudaStream_t)stream;
-    const rewl::SweepPlan plan = rewl::plan_sweep(M, sms, (size_t)optin);
-    if (plan.P < 1) return fail_static(REWL_ERR_ARG, "lattice too large for shared memory");
     rewl::Ctl ctl{};
     auto read_ctl = [&]() -> rewl_status {
         cudaError_t e2 = cudaMemcpyAsync(&ctl, S.ctl, sizeof ctl, cudaMemcpyDeviceToHost, s);
         if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(s);
-        if (e2 != cudaSuccess) return fail_static(REWL_ERR_CUDA, "status read: %s", cudaGetErrorString(e2));
-        if (ctl.error & rewl::ERR_OVERFLOW) return fail_static(REWL_ERR_OVERFLOW, "a histogram bin reached 2^31");
-        if (ctl.error & rewl::ERR_ENTRY) return fail_static(REWL_ERR_STATE, "a walker could not enter its window");
-        if (ctl.error & rewl::ERR_BOUNDS) return fail_static(REWL_ERR_STATE, "an index failed its bounds check (debug build)");
+        if (e2 != cudaSuccess) return rewl::host::fail(REWL_ERR_CUDA, "status read: %s", cudaGetErrorString(e2));
+        if (ctl.error & rewl::ERR_OVERFLOW) return rewl::host::fail(REWL_ERR_OVERFLOW, "a histogram bin reached 2^31");
+        if (ctl.error & rewl::ERR_ENTRY) return rewl::host::fail(REWL_ERR_STATE, "a walker could not enter its window");
+        if (ctl.error & rewl::ERR_BOUNDS)
+            return rewl::host::fail(REWL_ERR_STATE, "an index failed its bounds check (debug build)");
         if (ctl.error & rewl::ERR_ENERGY)
-            return fail_static(REWL_ERR_STATE, "a walker's energy differs from its recount (debug build)");
+            return rewl::host::fail(REWL_ERR_STATE, "a walker's energy differs from its recount (debug build)");
         return REWL_OK;
     };
 
     // everything the previous call left behind is cleared
-    cudaError_t e = cudaMemsetAsync(base, 0, total, s);
-    if (e == cudaSuccess) {
-        static_setup_kernel<<<(M.h + 127) / 128, 128, 0, s>>>(S.e_lo, S.lnf, M.h, M.N, M.W);
-        e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) e = rewl::launch_init(M, S, s);
+    // (zeroing, the window table, ln f = 1, the initial configurations: the
+    // same set-up as rewl_create_ext, into the array)
+    cudaError_t e = rewl::host::init_instance_async(h, s);
     if (e == cudaSuccess) e = rewl::prepare_sweep(M, plan);
-    if (e != cudaSuccess) return fail_static(REWL_ERR_CUDA, "initialisation: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) return rewl::host::fail(REWL_ERR_CUDA, "initialisation: %s", cudaGetErrorString(e));
     st = read_ctl();
     if (st) return st;
 
@@ -187,7 +149,7 @@ extern "C" rewl_status rewl_run_static(const rewl_params *prm, int spin_bits, lo
             if (e == cudaSuccess) e = rewl::launch_window_check(M, S, s);
             if (e == cudaSuccess) e = rewl::launch_exchange(M, S, s);
         }
-        if (e != cudaSuccess) return fail_static(REWL_ERR_CUDA, "launch: %s", cudaGetErrorString(e));
+        if (e != cudaSuccess) return rewl::host::fail(REWL_ERR_CUDA, "launch: %s", cudaGetErrorString(e));
         done_rounds += n;
         st = read_ctl();
         if (st) return st;
@@ -197,7 +159,8 @@ extern "C" rewl_status rewl_run_static(const rewl_params *prm, int spin_bits, lo
     e = cudaMemcpy2DAsync(lng_out, B * 8, S.lng, (size_t)M.m * B * 8, B * 8, hh, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess && mask_out) e = cudaMemcpyAsync(mask_out, S.mask, hh * B, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return fail_static(REWL_ERR_CUDA, "result copy: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) return rewl::host::fail(REWL_ERR_CUDA, "result copy: %s", cudaGetErrorString(e));
     if (converged) *converged = ctl.all_done ? 1 : 0;
     return REWL_OK;
+    REWL_API_CATCH
 }

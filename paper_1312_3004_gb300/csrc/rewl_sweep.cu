@@ -177,13 +177,29 @@ __device__ __forceinline__ long long exact_units(long long v, int e, bool &ok) {
 }
 
 // The reference decision in binary64: accept iff d >= 0 or u < exp(d), d = a - b.
-__device__ __noinline__ bool exact_accept(long long A, long long B, unsigned long long U, unsigned long long *ties) {
+// A draw with |u - exp(d)| < 1e-14 is a near tie: counted, and its step index
+// kept (the first two of the walker's launch) for the tie log.
+struct TieRec {
+    unsigned long long n, t[2];
+};
+__device__ __noinline__ bool exact_accept(long long A, long long B, unsigned long long U, TieRec *tie,
+                                          unsigned long long step) {
     const double d = __dsub_rn(__longlong_as_double(A), __longlong_as_double(B));
     if (d >= 0.0) return true;
     const double u = __ull2double_rn(U) * 0x1p-53;
     const double e = exp(d);
-    if (fabs(u - e) < 1e-14) *ties += 1ull;
+    if (fabs(u - e) < 1e-14) {
+        if (tie->n < 2ull) tie->t[tie->n] = step;
+        tie->n += 1ull;
+    }
     return u < e;
+}
+
+// The walker's near ties of this launch into the control block and the log.
+__device__ __forceinline__ void flush_ties(const State &S, int g, const TieRec &tie) {
+    if (!tie.n) return;
+    for (unsigned long long i = 0; i < tie.n && i < 2ull; ++i) record_tie(S.ctl, S.tlog, TIE_WL, (unsigned int)g, tie.t[i]);
+    if (tie.n > 2ull) atomicAdd(&S.ctl->ties, tie.n - 2ull);
 }
 
 __device__ __noinline__ long long exact_add(long long A, double lnf) {
@@ -214,7 +230,8 @@ constexpr int kMarkBits = 8192;
 constexpr long long kForceLo = -(1LL << 62);
 
 struct Tally {
-    unsigned long long ties, slow;
+    TieRec tie;
+    unsigned long long slow;
     unsigned int acc, seq;
 #ifdef REWL_DEBUG_CHECKS
     unsigned int bad = 0;  // failed bounds checks
@@ -338,7 +355,7 @@ __device__ void walker_sweep_1(const Model &M, uint32_t *__restrict__ lat, long 
             tally.slow += 1;
             const long long Ab = (AF & 1) ? lgb[REWL_IDX(Eo, 0, M.B, tally.bad)] : from_units(AF >> 1, ew);
             const long long Bb = (BF & 1) ? lgb[REWL_IDX(En, 0, M.B, tally.bad)] : from_units(BF >> 1, ew);
-            acc = dE == 0 ? true : exact_accept(Ab, Bb, cp.U, &tally.ties);
+            acc = dE == 0 ? true : exact_accept(Ab, Bb, cp.U, &tally.tie, t_io + (unsigned long long)i);
         }
         const long long cur = acc ? BF : AF;  // with dE = 0 both are the current shadow
         const int Eb2 = acc ? En : Eo;
@@ -677,7 +694,7 @@ __device__ void walker_sweep(const Model &M, uint32_t *__restrict__ lat, long lo
                 const unsigned long long kU = from_lane<S>(gm, U, kk);
                 const long long Ab = (AF & 1) ? lgb[REWL_IDX(Eo, 0, M.B, tally.bad)] : from_units(AF >> 1, ew);
                 const long long Bb = (BF & 1) ? lgb[REWL_IDX(En, 0, M.B, tally.bad)] : from_units(BF >> 1, ew);
-                acc = kdE == 0 ? true : exact_accept(Ab, Bb, kU, &tally.ties);
+                acc = kdE == 0 ? true : exact_accept(Ab, Bb, kU, &tally.tie, t_io + (unsigned long long)kk);
             }
             const long long cur = acc ? BF : AF;
             const int Eb2 = acc ? En : Eo;
@@ -764,7 +781,7 @@ __device__ void sweep_block(const Model &M, const State &Sg, int g0, int P, cons
     __syncthreads();
 
     const int grp = threadIdx.x / S, g = g0 + grp;
-    Tally tally{0ull, 0ull, 0u, 0u};
+    Tally tally{};
     if (grp < P && g < M.G && !Sg.done[g / M.m]) {
         unsigned char *base = smem + (size_t)grp * lay.stride;
         Stage st;
@@ -789,7 +806,7 @@ __device__ void sweep_block(const Model &M, const State &Sg, int g0, int P, cons
             atomicAdd(&Sg.ctl->flips, (unsigned long long)M.K);
             atomicAdd(&Sg.ctl->accepted, (unsigned long long)tally.acc);
             if (tally.slow) atomicAdd(&Sg.ctl->slow, tally.slow);
-            if (tally.ties) atomicAdd(&Sg.ctl->ties, tally.ties);
+            flush_ties(Sg, g, tally.tie);
             if (tally.seq) atomicAdd(&Sg.ctl->seq, (unsigned long long)tally.seq);
 #ifdef REWL_DEBUG_CHECKS
             if (tally.bad) atomicOr(&Sg.ctl->error, ERR_BOUNDS);
@@ -850,7 +867,7 @@ __global__ void __launch_bounds__(256) batch_walker_kernel(const InstDev *inst, 
     const Model Mr = M;
     const State Sr = Sg;
     Stage st{};
-    Tally tally{0ull, 0ull, 0u, 0u};
+    Tally tally{};
     const int w = g / Mr.m;
     const uint32_t c = Sr.slot_cfg[g];
     int E = Sr.cfg_E[c];
@@ -863,7 +880,7 @@ __global__ void __launch_bounds__(256) batch_walker_kernel(const InstDev *inst, 
     atomicAdd(&Sr.ctl->flips, (unsigned long long)Mr.K);
     atomicAdd(&Sr.ctl->accepted, (unsigned long long)tally.acc);
     if (tally.slow) atomicAdd(&Sr.ctl->slow, tally.slow);
-    if (tally.ties) atomicAdd(&Sr.ctl->ties, tally.ties);
+    flush_ties(Sr, g, tally.tie);
     if (tally.seq) atomicAdd(&Sr.ctl->seq, (unsigned long long)tally.seq);
 #ifdef REWL_DEBUG_CHECKS
     if (tally.bad) atomicOr(&Sr.ctl->error, ERR_BOUNDS);

@@ -16,12 +16,14 @@ _FIELD_DTYPES = {
     _lib.FIELD_MASK: np.uint8, _lib.FIELD_LNF: np.float64, _lib.FIELD_ITER: np.int32,
     _lib.FIELD_DONE: np.uint8, _lib.FIELD_ELO: np.int32, _lib.FIELD_ROUND: np.int64,
     _lib.FIELD_TRIPS: np.uint32, _lib.FIELD_TRIP_END: np.uint8, _lib.FIELD_PHASE: np.uint8,
+    _lib.FIELD_TIES: np.uint64,
 }
 FIELDS = {"spins": _lib.FIELD_SPINS, "energy": _lib.FIELD_ENERGY, "replica": _lib.FIELD_REPLICA,
           "steps": _lib.FIELD_STEPS, "lng": _lib.FIELD_LNG, "hist": _lib.FIELD_HIST,
           "mask": _lib.FIELD_MASK, "lnf": _lib.FIELD_LNF, "iter": _lib.FIELD_ITER,
           "done": _lib.FIELD_DONE, "e_lo": _lib.FIELD_ELO, "round": _lib.FIELD_ROUND,
-          "trips": _lib.FIELD_TRIPS, "trip_end": _lib.FIELD_TRIP_END, "phase": _lib.FIELD_PHASE}
+          "trips": _lib.FIELD_TRIPS, "trip_end": _lib.FIELD_TRIP_END, "phase": _lib.FIELD_PHASE,
+          "ties": _lib.FIELD_TIES}
 
 
 def _ptr(a):
@@ -144,7 +146,8 @@ class REWL:
                 _lib.FIELD_STEPS: (G,), _lib.FIELD_LNG: (G, B), _lib.FIELD_HIST: (G, B),
                 _lib.FIELD_MASK: (h, B), _lib.FIELD_LNF: (h,), _lib.FIELD_ITER: (h,),
                 _lib.FIELD_DONE: (h,), _lib.FIELD_ELO: (h,), _lib.FIELD_ROUND: (1,),
-                _lib.FIELD_TRIPS: (G,), _lib.FIELD_TRIP_END: (G,), _lib.FIELD_PHASE: (h,)}[field]
+                _lib.FIELD_TRIPS: (G,), _lib.FIELD_TRIP_END: (G,), _lib.FIELD_PHASE: (h,),
+                _lib.FIELD_TIES: (32, 2)}[field]
 
     def get(self, name):
         f = FIELDS[name]

@@ -3,9 +3,11 @@
 Both implement the same reading of Sec. 2 (arXiv:1312.3004) on the same
 Philox4x32-10 streams, so spins, energies, replica ids, step counters, ln g
 (bit for bit), histograms, masks and ln f must agree after every round.  A
-divergence is only acceptable when the library has recorded an acceptance
-draw with |u - exp(D)| < 1e-14, where exp of two different libraries may round
-the comparison differently.
+difference is accepted only when it is traced (tests/tie_trace.py): inverting
+near-tie decisions that the library logged (|u - exp(D)| < 1e-14, where exp of
+two libraries may round the comparison differently) in a fresh oracle run must
+reproduce the CUDA state exactly, and each such decision must be a near tie
+for the oracle too.
 """
 import numpy as np
 import pytest
@@ -13,6 +15,7 @@ import pytest
 from oracle import oracle as O
 from paper_1312_3004_gb300 import REWL, RewlError
 from paper_1312_3004_gb300 import workloads as WL
+from tie_trace import TracedPair, differing, gpu_state, gpu_ties, oracle_state, planted_near_tie
 
 pytestmark = pytest.mark.gpu
 
@@ -23,28 +26,21 @@ def make_pair(q, L, h, o, m, lnf_final, flat, K, seed, spin_bits=0):
     return gpu, orc
 
 
-def differences(gpu, orc):
-    diff = []
-    pairs = [("spins", orc.sigma()), ("energy", orc.E()), ("replica", orc.rep()), ("steps", orc.t()),
-             ("hist", orc.H()), ("mask", orc.mask()), ("iter", orc.iter()), ("done", orc.done()),
-             ("trips", orc.rt_trips()), ("trip_end", orc.rt_end())]
-    for name, want in pairs:
-        got = gpu.get(name)
-        if not np.array_equal(got, want):
-            diff.append(name)
-    for name, want in (("lng", orc.lng()), ("lnf", orc.lnf())):
-        if not np.array_equal(gpu.get(name).view(np.uint64), want.view(np.uint64)):
-            diff.append(name)
-    if gpu.round != orc.round:
-        diff.append("round")
-    return diff
+def traced(q, L, h, o, m, lnf_final, flat, K, seed, spin_bits=0, options=()):
+    """A TracedPair of a CUDA run (with the given rewl_set_option pairs) and the oracle."""
+    def make_gpu():
+        r = REWL(q, L, h, o, m, lnf_final, flat, K, seed, spin_bits=spin_bits)
+        for opt, val in options:
+            r.set_option(opt, val)
+        return r
+    return TracedPair(make_gpu, lambda: O.OracleREWL(q, L, h, o, m, lnf_final, flat, K, seed))
 
 
 def assert_parity(gpu, orc):
-    diff = differences(gpu, orc)
-    if diff:
-        ties = gpu.stats()["near_ties"]
-        assert ties > 0, "state differs in %s without a near-tie acceptance draw" % diff
+    """Strict equality, for tests that steer both sides by hand (set fields):
+    a difference there is reported with the library's near-tie log."""
+    diff = differing(gpu_state(gpu), oracle_state(orc))
+    assert not diff, "state differs in %s (near ties logged by the library: %s)" % (diff, gpu_ties(gpu))
 
 
 def run_both(gpu, orc, rounds):
@@ -75,10 +71,9 @@ def test_initial_state_matches(case):
 @pytest.mark.parametrize("case", SMALL)
 def test_rounds_match_bit_for_bit(case):
     *args, sb = case
-    gpu, orc = make_pair(*args, spin_bits=sb)
+    tp = traced(*args, spin_bits=sb)
     for n in (1, 2, 5, 12):
-        run_both(gpu, orc, n)
-        assert_parity(gpu, orc)
+        tp.run(n)
 
 
 SWEEPS = [("reference", 1, 0), ("lanes1", 0, 1), ("lanes2", 0, 2), ("lanes4", 0, 4), ("lanes8", 0, 8),
@@ -92,14 +87,11 @@ def test_every_sweep_variant_matches(case, sweep):
     width produce the oracle's states bit for bit."""
     from paper_1312_3004_gb300 import _lib
     *args, sb = case
-    gpu, orc = make_pair(*args, spin_bits=sb)
     _, kind, lanes = sweep
-    gpu.set_option(_lib.OPT_SWEEP_KERNEL, kind)
-    if kind == 0:
-        gpu.set_option(_lib.OPT_LANES, lanes)
+    opts = [(_lib.OPT_SWEEP_KERNEL, kind)] + ([(_lib.OPT_LANES, lanes)] if kind == 0 else [])
+    tp = traced(*args, spin_bits=sb, options=opts)
     for n in (1, 4, 10):
-        run_both(gpu, orc, n)
-        assert_parity(gpu, orc)
+        tp.run(n)
 
 
 @pytest.mark.parametrize("lanes", [1, 8, 32])
@@ -109,17 +101,13 @@ def test_lattices_in_global_memory_match(case, lanes):
     for large lattices, forced here at small sizes) gives the same states."""
     from paper_1312_3004_gb300 import _lib
     *args, sb = case
-    gpu, orc = make_pair(*args, spin_bits=sb)
-    gpu.set_option(_lib.OPT_LATTICE, 1)
-    gpu.set_option(_lib.OPT_LANES, lanes)
-    assert gpu.get_option(_lib.OPT_LATTICE) == 1
+    tp = traced(*args, spin_bits=sb, options=[(_lib.OPT_LATTICE, 1), (_lib.OPT_LANES, lanes)])
+    assert tp.test.get_option(_lib.OPT_LATTICE) == 1
     for n in (1, 4, 10):
-        run_both(gpu, orc, n)
-        assert_parity(gpu, orc)
-    gpu.set_option(_lib.OPT_LATTICE, 2)  # and back into shared memory mid-run
-    assert gpu.get_option(_lib.OPT_LATTICE) == 0
-    run_both(gpu, orc, 3)
-    assert_parity(gpu, orc)
+        tp.run(n)
+    tp.test.set_option(_lib.OPT_LATTICE, 2)  # and back into shared memory mid-run
+    assert tp.test.get_option(_lib.OPT_LATTICE) == 0
+    tp.run(3)
 
 
 def test_large_lattices_go_to_global_memory_and_match():
@@ -127,11 +115,10 @@ def test_large_lattices_go_to_global_memory_and_match():
     global memory, with hashed conflict marks (N > 8192); rounds against the
     oracle."""
     from paper_1312_3004_gb300 import _lib
-    gpu, orc = make_pair(10, 130, 8, 0.75, 1, 1e-6, 0.8, 2000, 3, spin_bits=8)
-    assert gpu.get_option(_lib.OPT_LATTICE) == 1
+    tp = traced(10, 130, 8, 0.75, 1, 1e-6, 0.8, 2000, 3, spin_bits=8)
+    assert tp.test.get_option(_lib.OPT_LATTICE) == 1
     for n in (1, 2):
-        run_both(gpu, orc, n)
-        assert_parity(gpu, orc)
+        tp.run(n)
 
 
 @pytest.mark.parametrize("lanes", [1, 8, 32])
@@ -140,38 +127,34 @@ def test_every_lane_width_converges_like_the_oracle(lanes):
     exact-add fallbacks): identical final state for each lane-group width."""
     from paper_1312_3004_gb300 import _lib
     args = (3, 5, 3, 0.75, 3, 1e-4, 0.8, 777, 5)
-    gpu, orc = make_pair(*args, spin_bits=4)
-    gpu.set_option(_lib.OPT_LANES, lanes)
-    assert orc.run(0) and gpu.run(0)
-    assert_parity(gpu, orc)
+    tp = traced(*args, spin_bits=4, options=[(_lib.OPT_LANES, lanes)])
+    tp.run(0)
+    assert tp.orc.all_done()
 
 
 def test_first_million_updates_per_walker_ising_L8():
     """10^6 WL updates per walker (100 rounds of 10^4) on the L=8 Ising workload."""
     p = WL.params("ising_L8")
     for seed in (1, 2):
-        gpu, orc = make_pair(*WL.rewl_args(p, seed), spin_bits=p["spin_bits"])
-        run_both(gpu, orc, 100)
-        assert orc.t().min() >= 10 ** 6 or orc.all_done()
-        assert_parity(gpu, orc)
+        tp = traced(*WL.rewl_args(p, seed), spin_bits=p["spin_bits"])
+        tp.run(100)
+        assert tp.orc.t().min() >= 10 ** 6 or tp.orc.all_done()
 
 
 def test_first_million_updates_per_walker_potts10_L20():
     p = WL.params("potts10_L20")
-    gpu, orc = make_pair(*WL.rewl_args(p, 1), spin_bits=p["spin_bits"])
-    run_both(gpu, orc, 100)
-    assert_parity(gpu, orc)
+    tp = traced(*WL.rewl_args(p, 1), spin_bits=p["spin_bits"])
+    tp.run(100)
 
 
 @pytest.mark.parametrize("seed", [1, 2, 3, 4])
 def test_converged_ising_L8_matches_oracle(seed):
     """Full runs to ln f < 1e-6: identical joined ln g and identical state."""
     p = WL.params("ising_L8")
-    gpu, orc = make_pair(*WL.rewl_args(p, seed), spin_bits=p["spin_bits"])
-    assert orc.run(0)
-    assert gpu.run(0)
-    assert_parity(gpu, orc)
-    a, b = gpu.lng(), orc.lng_joined()
+    tp = traced(*WL.rewl_args(p, seed), spin_bits=p["spin_bits"])
+    tp.run(0)
+    assert tp.orc.all_done()
+    a, b = tp.test.lng(), tp.orc.lng_joined()
     fin = np.isfinite(b)
     assert np.array_equal(np.isfinite(a), fin)
     assert np.max(np.abs(a[fin] - b[fin])) <= 1e-12
@@ -181,10 +164,9 @@ def test_large_potts10_L80_first_rounds_match():
     """The 1024-walker q=10, L=80 workload in the launch configuration the
     benchmark uses: initial state and two rounds agree with the oracle."""
     p = WL.params("potts10_L80")
-    gpu, orc = make_pair(*WL.rewl_args(p, 1), spin_bits=p["spin_bits"])
-    assert_parity(gpu, orc)
-    run_both(gpu, orc, 2)
-    assert_parity(gpu, orc)
+    tp = traced(*WL.rewl_args(p, 1), spin_bits=p["spin_bits"])
+    tp.check()
+    tp.run(2)
 
 
 def test_rounds_after_convergence_change_nothing():
@@ -277,12 +259,11 @@ def test_many_walkers_run_a_thread_each_with_global_state():
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     m = 256
     h = max(2, (80 * sms) // m + 1)
-    gpu, orc = make_pair(10, 12, h, 0.75, m, 1e-6, 0.8, 150, 21, spin_bits=8)
-    assert gpu.G > 80 * sms
-    assert gpu.get_option(_lib.OPT_LANES) == 1 and gpu.get_option(_lib.OPT_LATTICE) == 1
+    tp = traced(10, 12, h, 0.75, m, 1e-6, 0.8, 150, 21, spin_bits=8)
+    assert tp.test.G > 80 * sms
+    assert tp.test.get_option(_lib.OPT_LANES) == 1 and tp.test.get_option(_lib.OPT_LATTICE) == 1
     for n in (1, 2):
-        run_both(gpu, orc, n)
-        assert_parity(gpu, orc)
+        tp.run(n)
 
 
 def test_paper_size_workload_invariants():
@@ -313,3 +294,83 @@ def test_paper_size_workload_invariants():
         s = spins[g].reshape(L, L).astype(np.int32)
         recount = -int((s == np.roll(s, -1, axis=1)).sum() + (s == np.roll(s, -1, axis=0)).sum())
         assert recount == E[g], g
+
+
+PLANT = (3, 5, 2, 0.75, 2, 1e-3, 0.8, 200, 11)  # q=3, L=5: 2 windows of 2 walkers
+
+
+@pytest.mark.parametrize("sweep", [("reference", 1, 0), ("lanes1", 0, 1), ("lanes32", 0, 32)],
+                         ids=["reference", "lanes1", "lanes32"])
+def test_a_planted_near_tie_is_logged_and_traced(sweep):
+    """ln g set so that the first proposal of one walker has exp(D) within
+    1e-16 of its draw u: the library logs (WL step, walker, step 0), the
+    oracle sees the same near tie, and the states agree or differ by exactly
+    that decision, in every sweep variant."""
+    from paper_1312_3004_gb300 import _lib
+    seed = PLANT[-1]
+    for g in range(4):
+        if planted_near_tie(O.OracleREWL(*PLANT), seed, g):
+            break
+    else:
+        pytest.skip("no walker's first proposal stays in its window")
+    _, kind, lanes = sweep
+
+    def make_gpu():
+        r = REWL(*PLANT)
+        r.set_option(_lib.OPT_SWEEP_KERNEL, kind)
+        if kind == 0:
+            r.set_option(_lib.OPT_LANES, lanes)
+        planted_near_tie(O.OracleREWL(*PLANT), seed, g, setter=lambda lng: r.set("lng", lng))
+        return r
+
+    def make_orc():
+        o = O.OracleREWL(*PLANT)
+        planted_near_tie(o, seed, g)
+        return o
+
+    tp = TracedPair(make_gpu, make_orc)
+    tp.run(1)
+    n, log = gpu_ties(tp.test)
+    assert n >= 1 and (0, g, 0) in log
+    _, seen = tp.orc.ties()
+    assert any(e[:3] == (0, g, 0) and e[3] < 1e-14 for e in seen)
+    tp.run(3)
+
+
+def test_a_planted_exchange_near_tie_is_logged():
+    """Two windows of one walker each, both energies in the overlap: ln g of
+    walker 0 set so that Eq. 1's ln ratio D of the round-0 exchange equals ln u
+    of its draw.  The library logs (exchange, walker 0, round 0), the oracle
+    sees the same near tie, and the replica ids agree or differ by that
+    decision alone."""
+    from paper_1312_3004_gb300 import _lib
+    args = (3, 5, 2, 0.75, 1, 1e-3, 0.8, 200, 0)
+    for seed in range(1, 40):
+        a = args[:-1] + (seed,)
+        o = O.OracleREWL(*a)
+        E, lo, W = o.E(), o.e_lo(), o.W
+        if E[0] != E[1] and lo[1] <= E[0] <= lo[0] + W and lo[0] <= E[1] <= lo[0] + W:
+            break
+    else:
+        pytest.skip("no seed puts both walkers in the overlap")
+    r = O.philox4x32_10([0, 0, 0, 4], [seed & 0xffffffff, seed >> 32])
+    u = (((int(r[0]) >> 5) << 26) | (int(r[1]) >> 6)) * 2.0 ** -53
+    lng = o.lng()
+    lng[0, E[1] - lo[0]] = -np.log(u)  # D = (0 - ln g_0(E_1)) + 0 = ln u
+    o.set_lng(lng)
+    gpu = REWL(*a)
+    gpu.set("lng", lng)
+    gpu.run_phase(_lib.PHASE_EXCHANGE)
+    gpu.sync()
+    o.exchange()
+    n, log = gpu_ties(gpu)
+    assert n == 1 and log == [(1, 0, 0)]
+    _, seen = o.ties()
+    assert len(seen) == 1 and seen[0][:3] == (1, 0, 0) and seen[0][3] < 1e-14
+    got, want = gpu.get("replica"), o.rep()
+    if not np.array_equal(got, want):  # the two exps decided differently: the oracle's other choice
+        o2 = O.OracleREWL(*a)
+        o2.set_lng(lng)
+        o2.invert_decision(1, 0, 0)
+        o2.exchange()
+        assert np.array_equal(got, o2.rep())
