@@ -30,16 +30,24 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-# Algorithmic lane-operations of one WL proposal (integer / logic / shared-memory
-# slots that the method needs per flip; FP64 counted separately):
-#   Philox4x32-10 10 x (2 wide multiplies + 2 three-input XORs) + counter = 42
-#   site, new value, x/y split and 4 wrapped neighbour indices           = 14
-#   5 spin reads + 4-bit extraction                                      = 15
-#   dE (8 compares + 7 adds)                                             = 15
-#   window test 2, ln g reads 2, accept compare 1, u construction 4      =  9
-#   conditional spin write 3, ln g store 2, H read-add-store 3           =  8
-ALG_OPS_PER_FLIP = 103
-ALG_FP64_PER_FLIP = 2  # D = ln g(E) - ln g(E'), ln g(E) += ln f
+# Algorithmic operations of one WL proposal (what the method needs per flip,
+# not what a kernel issues), by the pipe that executes them:
+#   Philox4x32-10: 10 rounds x (2 wide multiplies [imad] + 2 three-input
+#     XORs [alu]) + 2 counter words [alu]
+#   site = r0 N >> 32, new value, y = s / L (high multiplies) and x = s - yL
+#     [imad 4]; four wrapped neighbour indices [alu 10]
+#   5 spin reads [lsu 5] and their 4-bit extraction [alu 10]
+#   dE: 8 compares + 7 adds [alu 15]
+#   window test 2, accept compare 1, u construction 4 [alu 7]; two ln g
+#     reads [lsu 2]
+#   conditional spin write [alu 2, lsu 1]; ln g store [lsu 1]; H read, add,
+#     store [lsu 2, alu 1]
+#   binary64: D = ln g(E) - ln g(E') and ln g(E) += ln f (2 adds), and exp(D)
+#     when D < 0, about 20 binary64 operations (a fraction rho_neg of the
+#     decisions, measured on the same workload by the oracle)
+OPS_PER_FLIP = {"imad": 24, "alu": 68, "lsu": 11}
+ALG_OPS_PER_FLIP = sum(OPS_PER_FLIP.values())  # 103 issue slots of integer / logic / shared-memory work
+FP64_PER_FLIP, FP64_PER_EXP = 2, 20
 SMS = 152
 LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
@@ -186,7 +194,9 @@ def cpu_baseline(p, seed, budget_s):
         t_run += time.perf_counter() - t0
         rounds += 1
     flips = rounds * walkers * p["exchange_interval"]
+    n_dec, n_neg = orc.decision_counts()
     return {"value": flips / t_run, "unit": "flips/s", "cores": 1, "kind": "oracle",
+            "rho_neg": n_neg / max(1, n_dec),
             "sample": "%d exchange round(s) of the %d-walker workload (%d WL proposals, %.1f s), "
                       "after a %.1f s set-up; single-threaded C" % (rounds, walkers, flips, t_run, t_create)}
 
@@ -255,7 +265,7 @@ def config_of(name, p):
 def run_ours(args):
     import torch
 
-    from paper_1312_3004_gb300 import REWL, _lib
+    from paper_1312_3004_gb300 import REWL, RewlError, _lib
     from paper_1312_3004_gb300 import workloads as WL
 
     rank, world, local = dist_env()
@@ -314,26 +324,77 @@ def run_ours(args):
     total_ms = sum(step_ms)
     flips = s1["flips"] - s0["flips"]
 
-    # end to end through the public call: rewl_run(1 round) reads the device
-    # status block back into host memory every step
-    e2e_steps = max(3, min(args.steps, 10))
-    e0s = r.stats()["flips"]
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        r.run(1)
-    e2e_s = time.perf_counter() - t0
-    e2e_flips = r.stats()["flips"] - e0s
+    # End to end through the public calls, on a second handle of the same seed
+    # and the same rounds (warm-up, then the timed ones) with the same L2
+    # flush before each: a step is rewl_run(handle, 1 round) -- which reads
+    # the device status block back -- and then the result into a host
+    # buffer: rewl_get_lng(partial) (copies walker 0's ln g of every window
+    # and the visited masks to the host and joins them), or, while some
+    # neighbouring windows share no visited bin yet, rewl_get_field(ln g of
+    # every walker).
+    import numpy as np
+
+    r2 = REWL(*WL.rewl_args(p, args.seed + rank), spin_bits=p["spin_bits"], stream=stream)
+    if args.schedule == "inv_t":
+        r2.set_option(_lib.OPT_SCHEDULE, _lib.SCHEDULE_INV_T)
+        r2.set("phase", 1)
+    for _ in range(args.warmup):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        r2.run_async(1)
+    r2.sync()
+    e2e_s, d2h, reads = 0.0, 0, {"rewl_get_lng": 0, "rewl_get_field": 0}
+    e0s = r2.stats()["flips"]
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        stream.synchronize()
+        t0 = time.perf_counter()
+        r2.run(1)
+        try:
+            res = r2.lng(partial=True)
+            d2h += 64 + p["h"] * r2.B * 9  # status, ln g rows and masks
+            reads["rewl_get_lng"] += 1
+        except RewlError:
+            res = r2.get("lng")
+            d2h += 64 + res.nbytes
+            reads["rewl_get_field"] += 1
+        e2e_s += time.perf_counter() - t0
+    e2e_flips = r2.stats()["flips"] - e0s
     e2e_local = e2e_flips / e2e_s
+    assert np.isfinite(res).any()
     total_ms_max, flips_all, e2e_val = reduce_over_ranks(dist, "cuda", total_ms, flips, e2e_local)
     value = flips_all / (total_ms_max / 1e3)
 
-    # roofline of the dominant kernel (sweep): algorithmic lane-ops per launch
+    # Roofline of the dominant kernel (the sweep): its proposals per launch /
+    # its mean launch time, against the per-flip bound of each pipe (measured
+    # issue rates x SMs x the SM clock sampled during the timed region /
+    # algorithmic operations per flip of that pipe); the binding one is the
+    # smallest.
+    from paper_1312_3004_gb300 import measure_pipes
+
+    pipes = measure_pipes()
     active_walkers = flips / max(1, args.steps) / p["exchange_interval"]
     sweep_avg_s = statistics.mean(sweep_ms) / 1e3
-    ops_per_launch = active_walkers * p["exchange_interval"] * ALG_OPS_PER_FLIP
-    achieved = ops_per_launch / sweep_avg_s / 1e12
-    peak = SMS * LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = active_walkers * p["exchange_interval"] / sweep_avg_s
+    f_hz = (clocks.get("sm_mhz") or pipes["max_clock_mhz"]) * 1e6
+    nsm = pipes["sms"]
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline and args.workload != "potts10_L300":
+        cpu = cpu_baseline(p, args.seed, args.cpu_seconds)
+    rho = cpu["rho_neg"] if cpu else 0.0  # unknown: no exp charged (the higher bound)
+    bounds = {
+        "issue": nsm * LANES_PER_SM * f_hz / ALG_OPS_PER_FLIP,
+        "imad": nsm * min(pipes["imad"], pipes["imad_hi"]) * f_hz / OPS_PER_FLIP["imad"],
+        "alu": nsm * min(pipes["lop3"], pipes["iadd"]) * f_hz / OPS_PER_FLIP["alu"],
+        "lsu": nsm * pipes["lds"] * f_hz / OPS_PER_FLIP["lsu"],
+        "fp64": nsm * pipes["dadd"] * f_hz / (FP64_PER_FLIP + FP64_PER_EXP * rho),
+    }
+    binding = min(bounds, key=bounds.get)
+    # each walker's steps form one dependent chain: the clock cycles one step
+    # of one walker takes, against the latency of the chain's shared-memory
+    # load and integer add
+    chain = active_walkers * f_hz / achieved if achieved > 0 else None
 
     if rank != 0:
         if dist:
@@ -345,21 +406,25 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": dict(config_of(args.workload, p), parallelism="replicas" if world > 1 else "single",
                                             lnf_schedule=args.schedule),
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                     "frac": achieved / peak,
+        "roofline": {"bound": binding, "achieved": achieved, "peak": bounds[binding], "unit": "flips/s",
+                     "frac": achieved / bounds[binding],
                      # the ncu figures were taken on the halving schedule's fast sweep
                      "traffic": TRAFFIC_PER_LAUNCH.get(args.workload) if args.schedule == "halving" else None,
                      "kernel": "sweep_fast_kernel" if r.get_option(_lib.OPT_SWEEP_KERNEL) == 0 else "sweep_kernel",
                      "avg_launch_ms": sweep_avg_s * 1e3,
-                     "ops_per_flip": ALG_OPS_PER_FLIP,
-                     "peak_basis": "152 SMs x 128 INT32/FP32 lanes x 2070 MHz (recipe unit counts)",
-                     # each walker's steps form one dependent chain: the clock cycles
-                     # one step of one walker takes (walkers x clock / flips per second)
-                     "chain_cycles_per_step": (active_walkers * (clocks.get("sm_mhz") or SM_MAX_MHZ) * 1e6
-                                               / (value / world)) if value > 0 else None,
+                     "bounds_flips_per_s": bounds,
+                     "ops_per_flip": dict(OPS_PER_FLIP, fp64=FP64_PER_FLIP + FP64_PER_EXP * rho),
+                     "rho_neg": rho if cpu else None,
+                     "pipes_per_clk_sm": {k: pipes[k] for k in ("dadd", "imad", "imad_hi", "lop3", "iadd", "lds")},
+                     "peak_basis": "measured issue rates (rewl_measure_pipes) x %d SMs x %.0f MHz (median SM clock "
+                                   "sampled in the timed region) / algorithmic operations per flip" % (nsm, f_hz / 1e6),
+                     "chain_cycles_per_step": chain,
+                     "latency_cycles": {k: pipes[k] for k in ("dadd_latency", "imad_latency", "lds_latency")},
                      "walkers": active_walkers},
-        "e2e": {"value": e2e_val, "unit": "flips/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 64,
-                "call": "rewl_run(handle, 1 round) incl. status read-back", "steps": e2e_steps},
+        "e2e": {"value": e2e_val, "unit": "flips/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": d2h / args.steps, "steps": args.steps, "reads": reads,
+                "call": "rewl_run(handle, 1 round) + rewl_get_lng(partial) into a host buffer, per step, on a "
+                        "second handle of the same seed over the same rounds, L2 flushed before each (untimed)"},
         "gpu_launches": 3 * args.steps,
         "sweep_plan": {"kernel": "fast" if r.get_option(_lib.OPT_SWEEP_KERNEL) == 0 else "reference",
                        "lanes_per_walker": r.get_option(_lib.OPT_LANES),
@@ -370,9 +435,9 @@ def run_ours(args):
         "wall_s_timed": wall,
         "sweep_share": sum(sweep_ms) / total_ms,
     }
-    if world == 1 and not args.no_cpu_baseline and args.workload != "potts10_L300":
-        line["cpu_baseline"] = cpu_baseline(p, args.seed, args.cpu_seconds)
-    elif args.workload == "potts10_L300":
+    if cpu:
+        line["cpu_baseline"] = cpu
+    if args.workload == "potts10_L300":
         # the oracle's window entry alone (2151 walkers, most of them quenched
         # down to their windows one proposal at a time) outlasts the budget
         line["cpu_baseline"] = None

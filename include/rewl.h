@@ -501,6 +501,25 @@ const char *rewl_last_error(void);
 /* Library version string.  No counterpart in the paper. */
 const char *rewl_version(void);
 
+/* ---- Measurement (no counterpart in the paper) ------------------------------
+ * Issue rates of the pipes a WL step uses, measured on the current device by
+ * micro-kernels (one CTA of 1024 threads per SM, eight independent chains of
+ * one PTX operation per thread, timed with the SM clock): lane-operations per
+ * clock per SM for add.rn.f64 (dadd), mad.lo.u32 (imad), mul.hi.u32
+ * (imad_hi), lop3.b32 (lop3), add.u32 (iadd) and conflict-free ld.shared.u32
+ * (lds); and the clocks of one dependent add.rn.f64, mad.lo.u32 and
+ * ld.shared.u32.  The per-flip roofline of the benchmark divides these rates
+ * by the method's per-flip operation counts.  Allocates and frees a few bytes
+ * of device memory; synchronises the device.  Errors: REWL_ERR_ARG (NULL),
+ * REWL_ERR_CUDA. */
+typedef struct rewl_pipe_rates {
+    double dadd, imad, imad_hi, lop3, iadd, lds;       /* per clock per SM  */
+    double dadd_latency, imad_latency, lds_latency;    /* clocks            */
+    int sms;                                           /* SMs of the device */
+    double max_clock_mhz;                              /* its maximum clock */
+} rewl_pipe_rates;
+rewl_status rewl_measure_pipes(rewl_pipe_rates *out);
+
 #ifdef __cplusplus
 }
 #endif

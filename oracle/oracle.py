@@ -82,6 +82,8 @@ def lib():
         L.orc_walker_visited_all.restype = i32
         L.orc_invert_decision.argtypes = [vp, i32, u64, u64]
         L.orc_invert_decision.restype = i32
+        L.orc_get_decision_counts.argtypes = [vp, vp]
+        L.orc_get_decision_counts.restype = None
         L.orc_get_ties.argtypes = [vp, vp, vp, i32]
         L.orc_get_ties.restype = i64
         L.ex_brute_force.argtypes = [i32, i32, vp]
@@ -232,6 +234,13 @@ class OracleREWL:
         n = int(lib().orc_get_ties(self._h, _ptr(ent), _ptr(gap), 64))
         k = min(n, 64)
         return n, [(int(a), int(b), int(c), float(d)) for (a, b, c), d in zip(ent[:k], gap[:k])]
+
+    def decision_counts(self):
+        """(WL decisions made, of which with D < 0): the proposals inside the
+        window, and those whose acceptance needed exp(D)."""
+        c = np.zeros(2, dtype=np.int64)
+        lib().orc_get_decision_counts(self._h, _ptr(c))
+        return int(c[0]), int(c[1])
 
     def set_schedule(self, schedule):
         """0: ln f halves per iteration (Sec. 2); 1: the 1/t rule."""

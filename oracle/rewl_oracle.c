@@ -120,6 +120,7 @@ static double orc_u53(uint32_t hi, uint32_t lo)
 typedef struct orc_decisions {
     int n_invert;
     uint64_t invert[ORC_MAX_INVERT][3];
+    int64_t n_wl, n_wl_neg;              /* WL decisions made; those with d < 0 */
     int64_t n_ties;                      /* near-tie draws seen (all of them)   */
     uint64_t tie[ORC_TIE_LOG][3];        /* first ORC_TIE_LOG: kind, who, when */
     double tie_gap[ORC_TIE_LOG];         /* |u - exp(d)| of each               */
@@ -224,6 +225,10 @@ enum { ORC_OK = 0, ORC_ERR_ARG = 1, ORC_ERR_NOMEM = 2, ORC_ERR_OVERFLOW = 5, ORC
 static int orc_decide(orc_rewl *s, int kind, uint64_t who, uint64_t when, double d, double u)
 {
     int acc = 1;
+    if (kind == 0) {
+        s->dec.n_wl += 1;
+        s->dec.n_wl_neg += d < 0.0;
+    }
     if (d < 0.0) {
         double e = exp(d);
         double gap = fabs(u - e);
@@ -250,6 +255,14 @@ int orc_invert_decision(orc_rewl *s, int kind, uint64_t who, uint64_t when)
     uint64_t *e = s->dec.invert[s->dec.n_invert++];
     e[0] = (uint64_t)kind; e[1] = who; e[2] = when;
     return ORC_OK;
+}
+
+/* WL acceptance decisions so far (proposals inside the window) and how many
+ * of them had d < 0, i.e. needed exp(d). */
+void orc_get_decision_counts(const orc_rewl *s, int64_t out[2])
+{
+    out[0] = s->dec.n_wl;
+    out[1] = s->dec.n_wl_neg;
 }
 
 /* Near-tie log: returns the number of near ties seen; fills up to `cap`

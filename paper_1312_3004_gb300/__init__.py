@@ -7,7 +7,7 @@ only marshals arguments.
 """
 from ._lib import RewlError, load  # noqa: F401
 from .rewl import (REWL, Batch, Server, bootstrap, canonical, canonical_distribution,  # noqa: F401
-                   equal_peak_temperature, ising_energy, join, specific_heat_peak)
+                   equal_peak_temperature, ising_energy, join, measure_pipes, specific_heat_peak)
 
 __all__ = ["REWL", "Batch", "Server", "RewlError", "load", "canonical", "canonical_distribution",
-           "specific_heat_peak", "equal_peak_temperature", "join", "bootstrap", "ising_energy"]
+           "specific_heat_peak", "equal_peak_temperature", "join", "bootstrap", "ising_energy", "measure_pipes"]

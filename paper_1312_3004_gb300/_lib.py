@@ -41,6 +41,13 @@ class Info(C.Structure):
                 ("device_bytes", C.c_size_t)]
 
 
+class PipeRates(C.Structure):
+    _fields_ = [("dadd", C.c_double), ("imad", C.c_double), ("imad_hi", C.c_double), ("lop3", C.c_double),
+                ("iadd", C.c_double), ("lds", C.c_double), ("dadd_latency", C.c_double),
+                ("imad_latency", C.c_double), ("lds_latency", C.c_double), ("sms", C.c_int),
+                ("max_clock_mhz", C.c_double)]
+
+
 class Stats(C.Structure):
     _fields_ = [("rounds", C.c_longlong), ("flips", C.c_longlong), ("accepted", C.c_longlong),
                 ("exch_tried", C.c_longlong), ("exch_accepted", C.c_longlong),
@@ -138,6 +145,8 @@ def load():
         getattr(L, name).restype = st
     L.rewl_last_error.argtypes = []
     L.rewl_last_error.restype = C.c_char_p
+    L.rewl_measure_pipes.argtypes = [C.POINTER(PipeRates)]
+    L.rewl_measure_pipes.restype = st
     L.rewl_version.argtypes = []
     L.rewl_version.restype = C.c_char_p
     _lib = L

@@ -393,3 +393,14 @@ def ising_energy(L, b):
     e = C.c_longlong()
     check(_lib.load().rewl_ising_energy(int(L), int(b), C.byref(e)))
     return e.value
+
+
+def measure_pipes():
+    """Issue rates of the WL step's pipes on the current device
+    (rewl_measure_pipes): lane-operations per clock per SM of f64 add,
+    32-bit multiply-add, high multiply, three-input logic, add and shared
+    load, the latencies of the dependent f64 add, multiply-add and shared
+    load in clocks, the SM count and the maximum SM clock (MHz)."""
+    r = _lib.PipeRates()
+    check(_lib.load().rewl_measure_pipes(C.byref(r)))
+    return {k: getattr(r, k) for k, _ in _lib.PipeRates._fields_}

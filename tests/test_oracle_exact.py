@@ -4,10 +4,16 @@ The generators are checked against each other (brute force vs transfer matrix,
 with and without the colour-permutation reduction), against closed-form counts
 derived by hand, against the total q^N, and -- for the Ising case q=2 --
 against Kaufman's exact partition function of the finite torus evaluated in
-high precision, which shares nothing with the transfer-matrix code.
+high precision, which shares nothing with the transfer-matrix code.  Beyond
+the transfer matrix's reach (L = 16, 32) the Ising counts come from Kaufman's
+function expanded as a polynomial (Beale's method, oracle/kaufman.py), checked
+against the transfer matrix where both run, against low-energy counts derived
+by hand, and used to pin the whole oracle on the 16 x 16 torus.
 """
 import math
+import os
 
+import numpy as np
 import pytest
 
 from oracle import oracle as O
@@ -92,3 +98,98 @@ def test_q10_exact_transition_temperature_constant():
     """The exact q=10 transition temperature quoted in Sec. 3.1 (0.701232) is
     1 / ln(1 + sqrt(q)) (self-duality); checks the constant the tests use."""
     assert abs(1.0 / math.log(1.0 + math.sqrt(10.0)) - 0.701232) < 5e-7
+
+
+# --------------------------------------------------------------------------
+# Beale's exact Ising density of states on larger tori (oracle/kaufman.py):
+# Kaufman's torus partition function expanded in y = exp(-2K).
+@pytest.mark.parametrize("L", [4, 6, 8])
+def test_kaufman_expansion_equals_the_transfer_matrix(L):
+    pytest.importorskip("mpmath")
+    from oracle import kaufman
+
+    counts, worst = kaufman.ising_counts(L)
+    assert worst < 1e-6
+    assert counts == O.exact_counts_tm(2, L)
+
+
+def _stored_exact():
+    import json
+    import os
+
+    path = os.path.join(os.path.dirname(__file__), "golden", "ising_exact_torus.json")
+    with open(path) as f:
+        return json.load(f)["lattices"]
+
+
+@pytest.mark.parametrize("L", [16, 32])
+def test_stored_exact_ising_counts_obey_closed_forms(L):
+    """The stored L = 16 and 32 counts (tests/golden/make_ising_exact.py):
+    exact integer rounding (residual far below 1/2); the low-energy counts
+    derived by hand for a torus without wrapping clusters, b broken bonds,
+    g(b) = 2 x (sets S of flipped spins with 4|S| - 2 adj(S) = b):
+    g(0) = 2; g(4) = 2N (one spin); g(6) = 4N (a domino); g(8) = N(N - 1) + 10N
+    (two spins not adjacent, straight and bent trominoes, the 2x2 square);
+    g(10) = 4N^2 + 24N (a domino and a spin not touching it, the 18 fixed
+    tetrominoes other than the square, the 8 P-pentominoes, the 2x3
+    rectangles); odd b and b = 2 impossible; sum g = 2^N; and g(b) = g(2N - b)."""
+    d = _stored_exact()[str(L)]
+    N = L * L
+    assert d["N"] == N and d["max_rounding_residual"] < 1e-6
+    low = [int(x) for x in d["low_counts"]]
+    assert low[:11] == [2, 0, 0, 0, 2 * N, 0, 4 * N, 0, N * (N - 1) + 10 * N, 0, 4 * N * N + 24 * N]
+    assert all(low[b] == 0 for b in range(1, 17, 2))
+    lng = d["lng"]
+    assert len(lng) == 2 * N + 1
+    for b in range(2 * N + 1):
+        assert (lng[b] is None) == (b % 2 == 1 or b in (2, 2 * N - 2))
+        assert lng[b] == lng[2 * N - b]
+    v = np.array([x for x in lng if x is not None])
+    top = v.max()
+    assert abs(top + math.log(np.exp(v - top).sum()) - N * math.log(2.0)) < 1e-12 * N
+
+
+@pytest.mark.parametrize("L", [16, 32])
+def test_stored_exact_ising_counts_give_kaufmans_partition_function(L):
+    """sum_b g(b) exp(-K (2b - 2N)) from the stored ln g equals Kaufman's
+    closed form evaluated in its usual real form (acosh of cosh g_k, signed
+    g_0) at temperatures on both sides of the transition."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 60
+    d = _stored_exact()[str(L)]
+    N = L * L
+    for K in (0.2, 0.4, 0.44068679, 0.5, 0.8):
+        terms = [mp.mpf(x) - mp.mpf(K) * (2 * b - 2 * N) for b, x in enumerate(d["lng"]) if x is not None]
+        top = max(terms)
+        ln_z = top + mp.log(sum(mp.exp(t - top) for t in terms))
+        assert abs(ln_z - mp.log(_kaufman_Z(K, L, mp))) < 1e-12 * N
+
+
+def _l16_run(seed):
+    import sys
+
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    from oracle import oracle as OO
+
+    o = OO.OracleREWL(2, 16, 4, 0.75, 2, 1e-6, 0.8, 10_000, seed)
+    assert o.run(0)
+    return o.lng_joined()
+
+
+def test_oracle_rewl_reproduces_the_exact_L16_ising_density_of_states():
+    """The whole oracle on the 16 x 16 Ising torus (4 windows, 75 % overlap,
+    2 walkers each, ln f_final = 1e-6): the visited energies are exactly the
+    exact support, and each run's normalised ln g is within the single-run
+    bound 0.35 of Beale's exact values (rms below 0.1)."""
+    import multiprocessing as mpr
+
+    d = _stored_exact()["16"]
+    ex = np.array([x if x is not None else -np.inf for x in d["lng"]])
+    fin = np.isfinite(ex)
+    with mpr.get_context("spawn").Pool(2) as pool:
+        runs = pool.map(_l16_run, [1, 2])
+    for lg in runs:
+        assert np.array_equal(np.isfinite(lg), fin)
+        err = lg[fin] - ex[fin]
+        assert np.abs(err).max() < 0.35
+        assert np.sqrt((err ** 2).mean()) < 0.1
