@@ -266,9 +266,43 @@ rewl_status rewl_get_field(rewl_t h, int field, void *out, size_t bytes);
 
 /* Overwrite one state array from host memory (same layouts as rewl_get_field;
  * REWL_FIELD_SPINS also recounts the energies; REWL_FIELD_ELO,
- * REWL_FIELD_REPLICA, REWL_FIELD_ENERGY and REWL_FIELD_TIES are read-only).  For tests that start from a chosen
- * state, e.g. fixed weights with ln f = 0. */
+ * REWL_FIELD_REPLICA, REWL_FIELD_ENERGY and REWL_FIELD_TIES are read-only).
+ * For tests that start from a chosen state, e.g. fixed weights with
+ * ln f = 0. */
 rewl_status rewl_set_field(rewl_t h, int field, const void *in, size_t bytes);
+
+/* ---- Fixed-weight production (Sec. 3.2) -------------------------------------
+ * After the density of states is estimated, the paper samples configurations
+ * with the fixed weights 1/g(E) and records distributions H(E, O) of
+ * observables.  For the Potts model the observable here is the majority count
+ * O = max_v #{i : s_i = v} in [ceil(N/q), N], kept in n_obins equal integer
+ * classes: class = (O - ceil(N/q)) * n_obins / (N - ceil(N/q) + 1).
+ *
+ * rewl_production_start: from the handle's current state (usually a converged
+ * run) every window keeps its walkers' own ln g and sets ln f = 0 (a WL step
+ * is then a Metropolis step with weights 1/g(E) inside the window), H is
+ * cleared and the histogram H(E, O) of every window is zeroed.  Allocates the
+ * histogram (h * (W + 1) * n_obins * 8 bytes) and spin counts (h * m * q * 4
+ * bytes) through the allocator hook.  May be called again to restart the
+ * histogram.  From then on rewl_run, rewl_run_async, rewl_run_phase,
+ * rewl_set_option, rewl_save and rewl_load return REWL_ERR_STATE.
+ * Errors: REWL_ERR_ARG (n_obins outside [1, N - ceil(N/q) + 1]),
+ * REWL_ERR_NOMEM, REWL_ERR_CUDA, REWL_ERR_STATE (instance of a batch).
+ *
+ * rewl_production_run: `rounds` production rounds, each K steps of every
+ * walker of every window (finished or not), each step followed by
+ * H(E, class) += 1 in its window's histogram, then a replica exchange with
+ * Eq. 1 between every pair (a, a + 1), a = round (mod 2), and round + 1.
+ * Synchronises the handle's stream.  Errors: REWL_ERR_STATE (not started),
+ * REWL_ERR_ARG (rounds < 0), REWL_ERR_CUDA.
+ *
+ * rewl_production_histogram: out[(w * (W + 1) + (E - E_lo(w))) * n_obins + class]
+ * = visits of window w (caller-owned host buffer, len = h * (W + 1) *
+ * n_obins), counted since rewl_production_start.  Errors: REWL_ERR_STATE
+ * (not started), REWL_ERR_ARG (len). */
+rewl_status rewl_production_start(rewl_t h, int n_obins);
+rewl_status rewl_production_run(rewl_t h, long long rounds);
+rewl_status rewl_production_histogram(rewl_t h, unsigned long long *out, size_t len);
 
 /* Checkpoint and resume (no counterpart in the paper).
  * Serialise the whole state (at a round boundary) into `buf` (host).  With

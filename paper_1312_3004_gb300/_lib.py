@@ -145,6 +145,11 @@ def load():
         getattr(L, name).restype = st
     L.rewl_last_error.argtypes = []
     L.rewl_last_error.restype = C.c_char_p
+    L.rewl_production_start.argtypes = [H, i32]
+    L.rewl_production_run.argtypes = [H, C.c_longlong]
+    L.rewl_production_histogram.argtypes = [H, vp, sz]
+    for name in ("rewl_production_start", "rewl_production_run", "rewl_production_histogram"):
+        getattr(L, name).restype = st
     L.rewl_measure_pipes.argtypes = [C.POINTER(PipeRates)]
     L.rewl_measure_pipes.restype = st
     L.rewl_version.argtypes = []

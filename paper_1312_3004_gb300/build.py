@@ -18,7 +18,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "librewl.so")
 LIB_DEBUG = os.path.join(OUT_DIR, "librewl_debug.so")
 SOURCES = ["rewl_kernels.cu", "rewl_sweep.cu", "rewl_host.cu", "rewl_batch.cu", "rewl_server.cu", "rewl_static.cu",
-           "rewl_analysis.cu", "rewl_probe.cu"]
+           "rewl_analysis.cu", "rewl_probe.cu", "rewl_production.cu"]
 HEADERS = ["rewl_internal.cuh", "rewl_host_internal.hpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -441,6 +441,7 @@ void rewl_set_allocator(void *(*alloc)(size_t bytes, void *ctx), void (*free_fn)
 void rewl_destroy(rewl_t h) {
     if (!h || !h->owns) return;  // instances of a batch belong to the batch
     if (h->stream) cudaStreamSynchronize(h->stream);
+    rewl::host::dev_free(h->prod_block);
     if (h->graph) cudaGraphExecDestroy(h->graph);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
     if (h->h_ctl) cudaFreeHost(h->h_ctl);
@@ -462,6 +463,7 @@ rewl_status rewl_run_async(rewl_t h, long long rounds) {
     REWL_API_TRY
     if (h && !h->owns) return fail(REWL_ERR_STATE, "this instance belongs to a batch: run the batch");
     if (!h) return fail(REWL_ERR_ARG, "NULL handle");
+    if (h->M.production) return fail(REWL_ERR_STATE, "in production: use rewl_production_run");
     if (rounds < 0) return fail(REWL_ERR_ARG, "rounds < 0");
     return enqueue_rounds(h, rounds);
     REWL_API_CATCH
@@ -474,6 +476,7 @@ rewl_status rewl_run_phase(rewl_t h, int phase) {
                                                               : "rewl_phase_exchange");
     if (h && !h->owns) return fail(REWL_ERR_STATE, "this instance belongs to a batch: run the batch");
     if (!h) return fail(REWL_ERR_ARG, "NULL handle");
+    if (h->M.production) return fail(REWL_ERR_STATE, "in production: use rewl_production_run");
     switch (phase) {
     case REWL_PHASE_SWEEP: REWL_CUDA(rewl::launch_sweep(h->M, h->S, h->plan, h->stream)); break;
     case REWL_PHASE_CHECK: REWL_CUDA(rewl::launch_window_check(h->M, h->S, h->stream)); break;
@@ -488,6 +491,7 @@ rewl_status rewl_set_option(rewl_t h, int option, long long value) {
     REWL_API_TRY
     if (h && !h->owns) return fail(REWL_ERR_STATE, "this instance belongs to a batch: run the batch");
     if (!h) return fail(REWL_ERR_ARG, "NULL handle");
+    if (h->M.production) return fail(REWL_ERR_STATE, "in production: options are fixed");
     int kind = h->plan.kind, lanes = h->plan.lanes, lat_mode = h->lat_mode;
     if (option == REWL_OPT_STALL_MS) {  // host side only: no re-plan
         if (value < 0) return fail(REWL_ERR_ARG, "stall limit %lld ms < 0", value);
@@ -556,6 +560,7 @@ rewl_status rewl_run(rewl_t h, long long max_rounds, int *converged) {
     const rewl::host::Range range("rewl_run");
     if (h && !h->owns) return fail(REWL_ERR_STATE, "this instance belongs to a batch: run the batch");
     if (!h) return fail(REWL_ERR_ARG, "NULL handle");
+    if (h->M.production) return fail(REWL_ERR_STATE, "in production: use rewl_production_run");
     long long left = max_rounds;
     rewl_status st = read_ctl(h);
     // stall watchdog: progress = iterations completed over all windows; a
@@ -758,6 +763,7 @@ rewl_status rewl_set_field(rewl_t h, int field, const void *in, size_t bytes) {
 rewl_status rewl_save(rewl_t h, void *buf, size_t *len) {
     REWL_API_TRY
     if (!h || !len) return fail(REWL_ERR_ARG, "NULL argument");
+    if (h->M.production) return fail(REWL_ERR_STATE, "in production: checkpoints hold WL runs only");
     size_t payload = 0;
     for (auto &p : h->parts) payload += p.bytes;
     const size_t need = sizeof(SaveHeader) + payload;
@@ -792,6 +798,7 @@ rewl_status rewl_save(rewl_t h, void *buf, size_t *len) {
 rewl_status rewl_load(rewl_t h, const void *buf, size_t len) {
     REWL_API_TRY
     if (!h || !buf) return fail(REWL_ERR_ARG, "NULL argument");
+    if (h->M.production) return fail(REWL_ERR_STATE, "in production: checkpoints hold WL runs only");
     if (len < sizeof(SaveHeader)) return fail(REWL_ERR_ARG, "blob too short");
     SaveHeader hd;
     std::memcpy(&hd, buf, sizeof hd);

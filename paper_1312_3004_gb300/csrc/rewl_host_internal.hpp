@@ -71,6 +71,8 @@ struct rewl_s {
     // false for an instance that lives inside a batch: the batch owns its
     // memory, stream and pinned status block, and runs its rounds
     bool owns = true;
+    // fixed-weight production (rewl_production_start): H(E, O) and spin counts
+    rewl::host::DevBlock prod_block;
 };
 
 namespace rewl {

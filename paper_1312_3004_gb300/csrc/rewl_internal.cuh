@@ -63,6 +63,8 @@ struct Model {
     long long K;              // WL steps per walker between exchanges
     double lnf_final, flatness;
     int schedule;             // ln f schedule: SCHED_HALVING or SCHED_INV_T
+    int production;           // 1: fixed-weight production (ln f = 0, H(E,O) kept, every window runs)
+    int n_obins;              // production: classes of the majority count O
 };
 
 // ln f schedules of the window check: halving per iteration (Sec. 2), or the
@@ -88,6 +90,8 @@ struct State {
                           // every walker's state in global memory
     uint8_t *phase;       // [h] 1/t rule: 1 once the window follows ln f = 1/t
     unsigned long long *tlog;  // [kTieLog][2] the first near-tie decisions: (kind << 32 | who, when)
+    unsigned long long *heo;   // production: [h][B][n_obins] visits H(E, O) of each window
+    int32_t *cnt;              // production: [G][q] spins of each value, by configuration buffer
     Ctl *ctl;             // control block
 };
 
@@ -158,6 +162,11 @@ cudaError_t prepare_sweep(const Model &M, const SweepPlan &p);
 cudaError_t launch_sweep(const Model &M, const State &S, const SweepPlan &p, cudaStream_t s);
 cudaError_t launch_window_check(const Model &M, const State &S, cudaStream_t s);
 cudaError_t launch_exchange(const Model &M, const State &S, cudaStream_t s);
+// Fixed-weight production (M.production = 1): the spin counts of every
+// configuration buffer, and K Metropolis steps with weights 1/g(E) per walker
+// with H(E, O) accumulated per window.
+cudaError_t launch_count_spins(const Model &M, const State &S, cudaStream_t s);
+cudaError_t launch_production_sweep(const Model &M, const State &S, cudaStream_t s);
 cudaError_t launch_set_spins(const Model &M, const State &S, const uint8_t *spins_dev, cudaStream_t s);
 cudaError_t launch_get_spins(const Model &M, const State &S, uint8_t *spins_dev, cudaStream_t s);
 size_t sweep_smem_per_walker(const Model &M);

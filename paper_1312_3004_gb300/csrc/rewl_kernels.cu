@@ -244,6 +244,100 @@ __global__ void __launch_bounds__(256) sweep_kernel(Model M, State S, int P) {
 }
 
 // ---------------------------------------------------------------------------
+// Fixed-weight production (Sec. 3.2: once g(E) is known, configurations are
+// sampled with the fixed weights 1/g(E) and distributions H(E, O) recorded).
+// Each walker keeps its own final ln g and ln f = 0, so a WL step is a
+// Metropolis step inside the window with the same decision as the sweep
+// (accept iff D >= 0 or u < exp(D)); after every step the window's H(E, O)
+// counts the current energy and the class of the majority count
+// O = max_v #{i : s_i = v} of the configuration, one of n_obins equal integer
+// classes of [ceil(N/q), N].  Every window runs, finished or not; H stays 0.
+// One thread per walker; lattice, ln g and the spin counts of the walker's
+// configuration buffer in global memory (the thread owns that buffer for the
+// launch); runs of equal (E, O) are added to H(E, O) with one atomic each.
+template <int BITS>
+__global__ void __launch_bounds__(128) production_kernel(Model M, State S) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= M.G) return;
+    const int w = g / M.m;
+    const int lo = S.e_lo[w], hi = lo + M.W;
+    const uint32_t c = S.slot_cfg[g];
+    uint32_t *lat = S.spins + (size_t)c * M.wpc;
+    int32_t *cnt = S.cnt + (size_t)c * M.q;
+    const double *lg = S.lng + (size_t)g * M.B;
+    unsigned long long *heo = S.heo + (size_t)w * M.B * M.n_obins;
+    int E = S.cfg_E[c];
+    unsigned long long t = S.t[g];
+    const int qlo = (M.N + M.q - 1) / M.q;  // ceil(N / q), the smallest majority
+    const long long span = (long long)(M.N - qlo + 1);
+    int nmax = 0;
+    for (int v = 0; v < M.q; ++v) nmax = max(nmax, cnt[v]);
+    int key = -1;                     // (bin, class) of the current run of steps
+    unsigned long long run = 0, n_acc = 0;
+    unsigned int bad = 0;  // failed bounds checks (debug build)
+    const uint32_t N = (uint32_t)M.N, qm1 = (uint32_t)(M.q - 1);
+    for (long long k = 0; k < M.K; ++k, ++t) {
+        const uint4 r = philox((uint32_t)t, (uint32_t)(t >> 32), (uint32_t)g, DOM_WL, M.key0, M.key1);
+        const int site = (int)__umulhi(r.x, N);
+        const int cur = spin_get<BITS>(lat, site);
+        const int v = (int)__umulhi(r.y, qm1);
+        const int nw = v + (v >= cur);
+        const int En = E + delta_e<BITS>(lat, neighbours(site, M.L, M.N, M.divL), cur, nw);
+        if (En >= lo && En <= hi) {
+            const double d = __dsub_rn(lg[REWL_IDX(E - lo, 0, M.B, bad)], lg[REWL_IDX(En - lo, 0, M.B, bad)]);
+            bool acc = d >= 0.0;
+            if (!acc) {
+                const double u = unit53(r.z, r.w);
+                const double e = exp(d);
+                acc = u < e;
+                if (fabs(u - e) < 1e-14) record_tie(S.ctl, S.tlog, TIE_WL, (unsigned int)g, t);
+            }
+            if (acc) {
+                spin_set<BITS>(lat, site, nw);
+                E = En;
+                ++n_acc;
+                const int oc = cnt[cur], nc = cnt[nw] + 1;
+                cnt[cur] = oc - 1;
+                cnt[nw] = nc;
+                if (nc > nmax) {
+                    nmax = nc;
+                } else if (oc == nmax) {  // the old majority value lost a spin
+                    nmax = 0;
+                    for (int u = 0; u < M.q; ++u) nmax = max(nmax, cnt[u]);
+                }
+            }
+        }
+        const int kk = REWL_IDX(E - lo, 0, M.B, bad) * M.n_obins + (int)((long long)(nmax - qlo) * M.n_obins / span);
+        if (kk == key) {
+            ++run;
+        } else {
+            if (run) atomicAdd(&heo[key], run);
+            key = kk;
+            run = 1;
+        }
+    }
+    if (run) atomicAdd(&heo[key], run);
+    S.cfg_E[c] = E;
+    S.t[g] = t;
+    atomicAdd(&S.ctl->flips, (unsigned long long)M.K);
+    atomicAdd(&S.ctl->accepted, n_acc);
+    if (bad) atomicOr(&S.ctl->error, ERR_BOUNDS);
+}
+
+// Spins of each value in configuration buffer blockIdx.x (production set-up).
+template <int BITS>
+__global__ void count_spins_kernel(Model M, State S) {
+    __shared__ int n[256];
+    const int c = blockIdx.x;
+    for (int v = threadIdx.x; v < 256; v += blockDim.x) n[v] = 0;
+    __syncthreads();
+    const uint32_t *lat = S.spins + (size_t)c * M.wpc;
+    for (int s = threadIdx.x; s < M.N; s += blockDim.x) atomicAdd(&n[spin_get<BITS>(lat, s)], 1);
+    __syncthreads();
+    for (int v = threadIdx.x; v < M.q; v += blockDim.x) S.cnt[(size_t)c * M.q + v] = n[v];
+}
+
+// ---------------------------------------------------------------------------
 // Barrier part 1, one CTA per window (Sec. 2): (a) bins any walker visited
 // join the window's mask; (b) walker k is flat iff min H >= p * mean H over the
 // mask; (c) when all m walkers are flat: ln g of every bin becomes the mean of
@@ -381,13 +475,13 @@ constexpr int XCH_THREADS = 1024;
 __device__ void exchange_block(const Model &M, const State &S) {
     __shared__ int perm[XCH_THREADS / 32][MAX_M];
     Ctl *ctl = S.ctl;
-    if (*(volatile unsigned int *)&ctl->all_done) return;
+    if (!M.production && *(volatile unsigned int *)&ctl->all_done) return;
     const unsigned long long round = ctl->round;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     const int m = M.m, B = M.B;
     unsigned long long tried = 0, acc = 0;
     for (int a = (int)(round & 1ull) + 2 * warp; a + 1 < M.h; a += 2 * nwarps) {
-        if (S.done[a] || S.done[a + 1]) continue;
+        if (!M.production && (S.done[a] || S.done[a + 1])) continue;  // production: every pair
         int *pi = perm[warp];
         if (lane == 0) {
             for (int k = 0; k < m; ++k) pi[k] = k;
@@ -592,6 +686,19 @@ cudaError_t launch_window_check(const Model &M, const State &S, cudaStream_t s) 
 
 cudaError_t launch_exchange(const Model &M, const State &S, cudaStream_t s) {
     exchange_kernel<<<1, XCH_THREADS, 0, s>>>(M, S);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_spins(const Model &M, const State &S, cudaStream_t s) {
+    if (M.bits == 8) count_spins_kernel<8><<<M.G, 256, 0, s>>>(M, S);
+    else count_spins_kernel<4><<<M.G, 256, 0, s>>>(M, S);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_production_sweep(const Model &M, const State &S, cudaStream_t s) {
+    const int threads = 128, grid = (M.G + threads - 1) / threads;
+    if (M.bits == 8) production_kernel<8><<<grid, threads, 0, s>>>(M, S);
+    else production_kernel<4><<<grid, threads, 0, s>>>(M, S);
     return cudaGetLastError();
 }
 

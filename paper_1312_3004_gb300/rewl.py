@@ -164,6 +164,21 @@ class REWL:
     def round(self):
         return int(self.get("round")[0])
 
+    def production_start(self, n_obins):
+        """Fixed weights 1/g(E) from the current ln g (ln f = 0) and a histogram
+        H(E, O) of the majority count in n_obins classes (Sec. 3.2)."""
+        check(self._L.rewl_production_start(self._h, n_obins))
+        self.n_obins = n_obins
+
+    def production_run(self, rounds):
+        check(self._L.rewl_production_run(self._h, rounds))
+
+    def heo(self):
+        """H(E, O) per window: uint64 [h][W + 1][n_obins]."""
+        a = np.zeros((self.h, self.B, self.n_obins), dtype=np.uint64)
+        check(self._L.rewl_production_histogram(self._h, _ptr(a), a.size))
+        return a
+
     def save(self):
         n = C.c_size_t(0)
         check(self._L.rewl_save(self._h, None, C.byref(n)))

@@ -5,6 +5,8 @@ import json
 import math
 import os
 
+import pytest
+
 from oracle import oracle as O
 from paper_1312_3004_gb300 import workloads as WL
 
@@ -153,3 +155,31 @@ def test_single_runs_lie_within_3_sigma_of_the_16_seed_mean_ising_L8():
     T_x, c_x = TH.specific_heat_peak(exact, 0.8, 2.0)
     se = d["sd"]["c_peak_T"] / 4.0
     assert abs(d["mean"]["c_peak_T"] - T_x) < 3 * se
+
+
+def test_stored_single_seed_runs_potts10_L20():
+    """tests/golden/potts10_L20_seed_lng.json (written by make_seed_lng.py
+    from the oracle alone): the exact joined ln g of seeds 1 and 2 is the
+    oracle's run summarised in potts10_L20_converged.json -- the same rounds,
+    the same support as the seed mean, sum g = q^N, ln g(ground) = ln q within
+    the spread, and the same specific-heat maximum."""
+    import numpy as np
+
+    from oracle import thermo as TH
+
+    seeds = load("potts10_L20_seed_lng.json")
+    summary = load("potts10_L20_converged.json")
+    N, q = 400, 10
+    tc_inf = 1.0 / math.log(1.0 + math.sqrt(q))
+    for run in seeds["runs"]:
+        mine = [r for r in summary["runs"] if r["seed"] == run["seed"]][0]
+        assert run["rounds"] == mine["rounds"]
+        lng = np.array([float.fromhex(x) for x in run["lng_hex"]])
+        fin = np.isfinite(lng)
+        assert np.array_equal(fin, np.array([m is not None for m in summary["lng_mean"]]))
+        top = lng[fin].max()
+        assert abs(top + math.log(np.exp(lng[fin] - top).sum()) - N * math.log(q)) < 1e-9
+        assert abs(lng[0] - math.log(q)) < 3 * summary["lng_sd"][0]
+        T, c = TH.specific_heat_peak(lng, 0.8 * tc_inf, 1.3 * tc_inf)
+        assert T == pytest.approx(mine["c_peak_T"], rel=1e-9)
+        assert c == pytest.approx(mine["c_peak"], rel=1e-9)
