@@ -642,13 +642,20 @@ def run_converge(args):
     p = WL.params(args.workload)
     seeds = [int(x) for x in args.converge.split(",") if x.strip()]
     runs = []
+    props = torch.cuda.get_device_properties(0)
+    uuid = getattr(props, "uuid", None)
+    uuid = ("GPU-" + str(uuid)) if uuid is not None and not str(uuid).startswith("GPU-") else uuid
+    sampler = ClockSampler(uuid if uuid else None)
+    sampler.start()
+    epoch0 = time.time()
     if args.concurrent:
         hs = [(seed, REWL(*WL.rewl_args(p, seed), spin_bits=p["spin_bits"], stream=torch.cuda.Stream()))
               for seed in seeds]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         finish = {}
-        el = 0.0
+        el, last = 0.0, 0.0
+        traces = {seed: [] for seed, _ in hs}
         while len(finish) < len(hs) and el < args.converge_limit:
             for seed, r in hs:
                 if seed not in finish:
@@ -656,13 +663,21 @@ def run_converge(args):
             for seed, r in hs:
                 if seed not in finish and r.sync():
                     finish[seed] = time.perf_counter() - t0
+                    print(json.dumps({"seed_converged": seed, "seconds": finish[seed]}), flush=True)
             el = time.perf_counter() - t0
+            if el - last >= 60.0:  # progress: windows done and the largest ln f left
+                last = el
+                for seed, r in hs:
+                    st = r.stats()
+                    traces[seed].append([round(el, 1), st["windows_done"], st["max_lnf"]])
+                print(json.dumps({"progress_s": round(el, 1), "seeds": {str(k): v[-1][1:] for k, v in traces.items()}}),
+                      flush=True)
         for seed, r in hs:
             s = r.stats()
             secs = finish.get(seed, el)
             runs.append({"seed": seed, "converged": seed in finish, "seconds": secs, "rounds": s["rounds"],
                          "flips": s["flips"], "mean_flips_per_s": s["flips"] / secs,
-                         "windows_done": s["windows_done"], "progress": [],
+                         "windows_done": s["windows_done"], "progress": traces[seed],
                          "analysis": analyse(r, p) if seed in finish else None})
             runs[-1]["oracle"] = oracle_reference(args.workload, seed, runs[-1]["analysis"],
                                                   r.lng() if seed in finish else None)
@@ -688,8 +703,9 @@ def run_converge(args):
         runs[-1]["oracle"] = oracle_reference(args.workload, seed, runs[-1]["analysis"], r.lng() if conv else None)
         print(json.dumps({"seed_done": runs[-1]}), flush=True)
         r.close()
+    clocks = sampler.stop(epoch0, time.time())
     done = [x["seconds"] for x in runs if x["converged"]]
-    line = {"metric": "time to converge", "value": statistics.median(done) if len(done) == len(runs) else None,
+    line = {"metric": "time to converge", "clocks": clocks, "value": statistics.median(done) if len(done) == len(runs) else None,
             "unit": "s", "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
             "config": config_of(args.workload, p), "seeds": seeds,
             "min_s": min(done) if done else None, "max_s": max(done) if done else None,

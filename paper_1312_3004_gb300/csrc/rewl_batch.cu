@@ -19,7 +19,6 @@ using rewl::host::fail;
 namespace {
 
 constexpr int kBatchGraphRounds = 4;
-constexpr size_t kCtaBudget = 72 * 1024;  // shared memory per sweep CTA (3 CTAs per SM)
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -28,6 +27,15 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
         cudaError_t e_ = (call);                                                                \
         if (e_ != cudaSuccess) return fail(REWL_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
+
+// A mapping of the batch's walkers to threads, and the spin packing: none of it
+// changes a result (every choice runs the same block code on the same state).
+struct Config {
+    int bits = 8;           // spins per configuration word: 4 or 8 bits each
+    int lanes = 32;         // 32: lane groups, state staged in shared memory; 1: a thread per walker
+    int cta_kb = 72;        // lanes 32: shared memory per sweep CTA (walkers per CTA follow)
+    int threads = 256;      // lanes 1: threads per CTA
+};
 
 struct SweepClass {
     int bits = 4, lanes = 32, threads = 0, grid = 0;
@@ -46,12 +54,14 @@ constexpr long long kWalkerModeMin = 16384;
 
 struct rewl_batch_s {
     std::vector<rewl_s *> inst;
-    void *dmem = nullptr;
+    void *dmem = nullptr;         // instances and their control blocks
     rewl::host::DevBlock dblock;
     size_t dbytes = 0;
     rewl::Ctl *h_ctls = nullptr;  // pinned mirrors of every instance's control block
     rewl::Ctl *d_ctls = nullptr;  // the control blocks, contiguous
     cudaStream_t own_stream = nullptr, stream = nullptr;
+    // tables of the current configuration (rebuilt by configure)
+    rewl::host::DevBlock tblock;
     rewl::InstDev *d_inst = nullptr;
     rewl::WinItem *d_wins = nullptr;
     int n_wins = 0;
@@ -59,6 +69,11 @@ struct rewl_batch_s {
     unsigned int *d_queues = nullptr;
     cudaGraphExec_t graph = nullptr;
     int sms = 0;
+    Config cfg;
+    bool bits_free = false;   // the packing may change (spin_bits = 0 and every q <= 16)
+    bool lanes_free = false;  // the mapping may change (lanes = 0)
+    bool fits32[2] = {true, true};  // every walker fits a lane group's shared memory at 4 / 8 bits
+    size_t bytes_config = 0;
 };
 
 namespace {
@@ -133,8 +148,135 @@ void destroy_batch(rewl_batch_s *b) {
     for (rewl_s *h : b->inst) delete h;
     if (b->own_stream) cudaStreamDestroy(b->own_stream);
     if (b->h_ctls) cudaFreeHost(b->h_ctls);
+    rewl::host::dev_free(b->tblock);
     rewl::host::dev_free(b->dblock);
     delete b;
+}
+
+// Spins of every instance repacked to `bits` per spin, in place: each
+// instance's configurations are unpacked to bytes in a scratch buffer and
+// packed again (the buffers were sized for 8-bit packing).
+rewl_status repack(rewl_batch_s *b, int bits) {
+    size_t need = 0;
+    for (rewl_s *h : b->inst) need = std::max(need, (size_t)h->M.G * (size_t)h->M.N);
+    rewl::host::DevBlock scratch;
+    cudaError_t e = rewl::host::dev_alloc(scratch, need);
+    if (e != cudaSuccess) return fail(REWL_ERR_NOMEM, "repacking scratch (%zu bytes): %s", need, cudaGetErrorString(e));
+    for (rewl_s *h : b->inst) {
+        if (h->M.bits == bits) continue;
+        e = rewl::launch_get_spins(h->M, h->S, (uint8_t *)scratch.ptr, b->stream);
+        if (e != cudaSuccess) break;
+        h->M.bits = bits;
+        h->M.wpc = (h->M.N * bits + 31) / 32;
+        e = rewl::launch_set_spins(h->M, h->S, (const uint8_t *)scratch.ptr, b->stream);
+        if (e != cudaSuccess) break;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    rewl::host::dev_free(scratch);
+    if (e != cudaSuccess) return fail(REWL_ERR_CUDA, "repacking: %s", cudaGetErrorString(e));
+    return REWL_OK;
+}
+
+// Builds the tables, work lists, launch shapes and graph of configuration c
+// (repacking the spins first if its packing differs).
+rewl_status configure(rewl_batch_s *b, const Config &c) {
+    BATCH_CUDA(cudaStreamSynchronize(b->stream));
+    if (c.bits != b->cfg.bits || b->classes.empty()) {
+        bool differ = false;
+        for (rewl_s *h : b->inst) differ = differ || h->M.bits != c.bits;
+        if (differ) {
+            rewl_status st = repack(b, c.bits);
+            if (st) return st;
+        }
+    }
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    const int n = (int)b->inst.size();
+    std::vector<rewl::InstDev> tab((size_t)n);
+    std::vector<rewl::WinItem> wins;
+    for (int i = 0; i < n; ++i)
+        for (int w = 0; w < b->inst[(size_t)i]->M.h; ++w) wins.push_back({i, w});
+    b->n_wins = (int)wins.size();
+    b->classes.clear();
+    const size_t budget = (size_t)c.cta_kb * 1024;
+    for (int i = 0; i < n; ++i) {
+        rewl_s *h = b->inst[(size_t)i];
+        tab[(size_t)i].M = h->M;
+        tab[(size_t)i].S = h->S;
+        tab[(size_t)i].lay = rewl::fast_layout(h->M, c.lanes, c.lanes == 1);
+        int cls = -1;
+        for (size_t k = 0; k < b->classes.size(); ++k)
+            if (b->classes[k].bits == h->M.bits) cls = (int)k;
+        if (cls < 0) {
+            SweepClass sc;
+            sc.bits = h->M.bits;
+            sc.lanes = c.lanes;
+            b->classes.push_back(sc);
+            cls = (int)b->classes.size() - 1;
+        }
+        SweepClass &sc = b->classes[(size_t)cls];
+        if (c.lanes == 1) {
+            for (int g = 0; g < h->M.G; ++g) sc.walkers.push_back({i, g});
+            continue;
+        }
+        const rewl::Layout &lay = tab[(size_t)i].lay;
+        int P = (int)(std::max(budget, (size_t)lay.stride) / (size_t)lay.stride);
+        P = std::min(P, 256 / sc.lanes);
+        for (int g0 = 0; g0 < h->M.G; g0 += P) sc.items.push_back({i, g0, std::min(P, h->M.G - g0), 0});
+        sc.smem = std::max(sc.smem, (size_t)P * (size_t)lay.stride);
+        sc.threads = std::max(sc.threads, P * sc.lanes);
+    }
+    size_t off = 0;
+    const size_t off_tab = off;
+    off += align256((size_t)n * sizeof(rewl::InstDev));
+    const size_t off_wins = off;
+    off += align256(wins.size() * sizeof(rewl::WinItem));
+    std::vector<size_t> off_items;
+    for (auto &k : b->classes) {
+        off_items.push_back(off);
+        off += align256(k.lanes == 1 ? k.walkers.size() * sizeof(rewl::WalkerItem)
+                                     : k.items.size() * sizeof(rewl::SweepItem));
+    }
+    const size_t off_q = off;
+    off += align256(b->classes.size() * sizeof(unsigned int));
+    rewl::host::dev_free(b->tblock);
+    cudaError_t e = rewl::host::dev_alloc(b->tblock, off);
+    if (e != cudaSuccess) return fail(REWL_ERR_NOMEM, "batch tables (%zu bytes): %s", off, cudaGetErrorString(e));
+    b->bytes_config = off;
+    char *base = (char *)b->tblock.ptr;
+    b->d_inst = (rewl::InstDev *)(base + off_tab);
+    b->d_wins = (rewl::WinItem *)(base + off_wins);
+    b->d_queues = (unsigned int *)(base + off_q);
+    e = cudaMemcpyAsync(b->d_inst, tab.data(), tab.size() * sizeof(rewl::InstDev), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_wins, wins.data(), wins.size() * sizeof(rewl::WinItem), cudaMemcpyHostToDevice, b->stream);
+    for (size_t k = 0; k < b->classes.size() && e == cudaSuccess; ++k) {
+        SweepClass &sc = b->classes[k];
+        sc.d_queue = b->d_queues + k;
+        if (sc.lanes == 1) {
+            sc.d_walkers = (rewl::WalkerItem *)(base + off_items[k]);
+            e = cudaMemcpyAsync(sc.d_walkers, sc.walkers.data(), sc.walkers.size() * sizeof(rewl::WalkerItem),
+                                cudaMemcpyHostToDevice, b->stream);
+            sc.threads = c.threads;
+            sc.grid = (int)((sc.walkers.size() + (size_t)c.threads - 1) / (size_t)c.threads);
+            continue;
+        }
+        sc.d_items = (rewl::SweepItem *)(base + off_items[k]);
+        e = cudaMemcpyAsync(sc.d_items, sc.items.data(), sc.items.size() * sizeof(rewl::SweepItem),
+                            cudaMemcpyHostToDevice, b->stream);
+        if (e != cudaSuccess) break;
+        e = rewl::launch_batch_sweep(sc.bits, sc.lanes, nullptr, nullptr, 0, nullptr, 0, sc.threads, sc.smem, nullptr,
+                                     true);
+        if (e != cudaSuccess) break;
+        const int per_sm = std::max(1, rewl::batch_sweep_ctas_per_sm(sc.bits, sc.lanes, sc.threads, sc.smem));
+        sc.grid = std::min((int)sc.items.size(), per_sm * b->sms);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // tab and wins live on this frame
+    if (e != cudaSuccess) return fail(REWL_ERR_CUDA, "batch configuration: %s", cudaGetErrorString(e));
+    b->cfg = c;
+    return build_batch_graph(b);
 }
 
 }  // namespace
@@ -159,71 +301,44 @@ rewl_status rewl_batch_create_ext(const rewl_params *jobs, int n, int spin_bits,
     };
     // ---- instances: parameters, sizes, plans -----------------------------------
     long long walkers = 0;
-    for (int i = 0; i < n; ++i) walkers += (long long)std::max(jobs[i].h, 0) * std::max(jobs[i].m, 0);
-    if (lanes == 0) lanes = walkers >= kWalkerModeMin ? 1 : 32;
+    bool small_q = true;
+    for (int i = 0; i < n; ++i) {
+        walkers += (long long)std::max(jobs[i].h, 0) * std::max(jobs[i].m, 0);
+        small_q = small_q && jobs[i].q <= 16;
+    }
+    b->lanes_free = lanes == 0;
+    b->bits_free = spin_bits == 0 && small_q;
+    Config c;
+    c.lanes = lanes != 0 ? lanes : (walkers >= kWalkerModeMin ? 1 : 32);
     // a thread per walker reads whole bytes faster than 4-bit fields
-    const int bits = (spin_bits == 0 && lanes == 1) ? 8 : spin_bits;
+    c.bits = spin_bits != 0 ? spin_bits : ((c.lanes == 1 || !small_q) ? 8 : 4);
     size_t off = 0;
     std::vector<size_t> inst_off((size_t)n);
     for (int i = 0; i < n; ++i) {
         rewl_s *h = new rewl_s();
         h->owns = false;
         b->inst.push_back(h);
-        rewl_status st = rewl::host::prepare_instance(h, jobs[i], bits, 32);
+        rewl_status st = rewl::host::prepare_instance(h, jobs[i], c.bits, 32, b->bits_free ? 8 : 0);
         if (st) return cleanup(fail(st, "job %d: %s", i, rewl_last_error()));
         inst_off[(size_t)i] = off;
         off += align256(h->dbytes);
     }
-    for (int i = 0; i < n && lanes == 32; ++i) {
+    for (int i = 0; i < n; ++i) {  // a lane group's shared memory at either packing
         rewl_s *h = b->inst[(size_t)i];
-        if ((size_t)h->plan.P < 1 || rewl::fast_smem_per_walker(h->M, 32) > (size_t)h->smem_optin)
-            return cleanup(fail(REWL_ERR_ARG, "job %d: a walker does not fit in shared memory", i));
+        for (int k = 0; k < 2; ++k) {
+            rewl::Model mk = h->M;
+            mk.bits = k ? 8 : 4;
+            mk.wpc = (mk.N * mk.bits + 31) / 32;
+            if (rewl::fast_smem_per_walker(mk, 32) > (size_t)h->smem_optin) b->fits32[k] = false;
+        }
+    }
+    if (c.lanes == 32 && !b->fits32[c.bits == 8]) {
+        if (!b->lanes_free) return cleanup(fail(REWL_ERR_ARG, "a walker does not fit in shared memory"));
+        c.lanes = 1;
     }
     b->sms = b->inst[0]->sms;
-    // ---- tables -------------------------------------------------------------
-    std::vector<rewl::InstDev> tab((size_t)n);
-    std::vector<rewl::WinItem> wins;
-    for (int i = 0; i < n; ++i)
-        for (int w = 0; w < b->inst[(size_t)i]->M.h; ++w) wins.push_back({i, w});
-    b->n_wins = (int)wins.size();
-    for (int i = 0; i < n; ++i) {
-        rewl_s *h = b->inst[(size_t)i];
-        const rewl::Layout lay = rewl::fast_layout(h->M, 32);
-        int cls = -1;
-        for (size_t c = 0; c < b->classes.size(); ++c)
-            if (b->classes[c].bits == h->M.bits) cls = (int)c;
-        if (cls < 0) {
-            SweepClass c;
-            c.bits = h->M.bits;
-            c.lanes = lanes;
-            b->classes.push_back(c);
-            cls = (int)b->classes.size() - 1;
-        }
-        SweepClass &c = b->classes[(size_t)cls];
-        if (lanes == 1) {
-            for (int g = 0; g < h->M.G; ++g) c.walkers.push_back({i, g});
-            continue;
-        }
-        int P = (int)(std::max(kCtaBudget, (size_t)lay.stride) / (size_t)lay.stride);
-        P = std::min(P, 256 / c.lanes);
-        for (int g0 = 0; g0 < h->M.G; g0 += P) c.items.push_back({i, g0, std::min(P, h->M.G - g0), 0});
-        c.smem = std::max(c.smem, (size_t)P * (size_t)lay.stride);
-        c.threads = std::max(c.threads, P * c.lanes);
-    }
     const size_t off_ctl = off;
     off += align256((size_t)n * sizeof(rewl::Ctl));
-    const size_t off_tab = off;
-    off += align256((size_t)n * sizeof(rewl::InstDev));
-    const size_t off_wins = off;
-    off += align256(wins.size() * sizeof(rewl::WinItem));
-    std::vector<size_t> off_items;
-    for (auto &c : b->classes) {
-        off_items.push_back(off);
-        off += align256(c.lanes == 1 ? c.walkers.size() * sizeof(rewl::WalkerItem)
-                                     : c.items.size() * sizeof(rewl::SweepItem));
-    }
-    const size_t off_q = off;
-    off += align256(b->classes.size() * sizeof(unsigned int));
     b->dbytes = off;
     cudaError_t e = rewl::host::dev_alloc(b->dblock, off);
     if (e != cudaSuccess)
@@ -236,9 +351,6 @@ rewl_status rewl_batch_create_ext(const rewl_params *jobs, int n, int spin_bits,
     if (e != cudaSuccess) return cleanup(fail(REWL_ERR_NOMEM, "cudaMallocHost: %s", cudaGetErrorString(e)));
     char *base = (char *)b->dmem;
     b->d_ctls = (rewl::Ctl *)(base + off_ctl);
-    b->d_inst = (rewl::InstDev *)(base + off_tab);
-    b->d_wins = (rewl::WinItem *)(base + off_wins);
-    b->d_queues = (unsigned int *)(base + off_q);
     // ---- carve and initialise every instance ---------------------------------
     e = cudaMemsetAsync(b->d_ctls, 0, (size_t)n * sizeof(rewl::Ctl), b->stream);
     for (int i = 0; i < n && e == cudaSuccess; ++i) {
@@ -247,40 +359,14 @@ rewl_status rewl_batch_create_ext(const rewl_params *jobs, int n, int spin_bits,
         h->S.ctl = b->d_ctls + i;  // control blocks contiguous: one status read for all
         h->stream = b->stream;
         h->h_ctl = b->h_ctls + i;
-        tab[(size_t)i].M = h->M;
-        tab[(size_t)i].S = h->S;
-        tab[(size_t)i].lay = rewl::fast_layout(h->M, lanes, lanes == 1);
         e = rewl::host::init_instance_async(h, b->stream);
-    }
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->d_inst, tab.data(), tab.size() * sizeof(rewl::InstDev), cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->d_wins, wins.data(), wins.size() * sizeof(rewl::WinItem), cudaMemcpyHostToDevice, b->stream);
-    for (size_t c = 0; c < b->classes.size() && e == cudaSuccess; ++c) {
-        SweepClass &k = b->classes[c];
-        k.d_queue = b->d_queues + c;
-        if (k.lanes == 1) {
-            k.d_walkers = (rewl::WalkerItem *)(base + off_items[c]);
-            e = cudaMemcpyAsync(k.d_walkers, k.walkers.data(), k.walkers.size() * sizeof(rewl::WalkerItem),
-                                cudaMemcpyHostToDevice, b->stream);
-            k.threads = 256;
-            k.grid = (int)((k.walkers.size() + 255) / 256);
-            continue;
-        }
-        k.d_items = (rewl::SweepItem *)(base + off_items[c]);
-        e = cudaMemcpyAsync(k.d_items, k.items.data(), k.items.size() * sizeof(rewl::SweepItem), cudaMemcpyHostToDevice,
-                            b->stream);
-        if (e != cudaSuccess) break;
-        e = rewl::launch_batch_sweep(k.bits, k.lanes, nullptr, nullptr, 0, nullptr, 0, k.threads, k.smem, nullptr, true);
-        if (e != cudaSuccess) break;
-        const int per_sm = std::max(1, rewl::batch_sweep_ctas_per_sm(k.bits, k.lanes, k.threads, k.smem));
-        k.grid = std::min((int)k.items.size(), per_sm * b->sms);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return cleanup(fail(REWL_ERR_CUDA, "batch set-up: %s", cudaGetErrorString(e)));
     rewl_status st = read_batch_status(b, nullptr);
     if (st) return cleanup(st);
-    st = build_batch_graph(b);
+    b->cfg = c;
+    st = configure(b, c);
     if (st) return cleanup(st);
     *out = b;
     return REWL_OK;

@@ -289,7 +289,7 @@ void set_allocator(void *(*alloc)(size_t, void *), void (*free_fn)(void *, void 
     g_alloc.ctx = alloc ? ctx : nullptr;
 }
 
-rewl_status prepare_instance(rewl_s *h, const rewl_params &p, int spin_bits, int lanes) {
+rewl_status prepare_instance(rewl_s *h, const rewl_params &p, int spin_bits, int lanes, int spin_capacity_bits) {
     rewl_status st = check_params(p, spin_bits);
     if (st) return st;
     std::vector<int32_t> e_lo;
@@ -325,7 +325,9 @@ rewl_status prepare_instance(rewl_s *h, const rewl_params &p, int spin_bits, int
         return fail(REWL_ERR_ARG, "one walker needs %zu bytes of shared memory (> %d)",
                     rewl::fast_smem_per_walker(M, h->plan.lanes, h->plan.lat_global != 0), h->smem_optin);
     const size_t G = (size_t)M.G, B = (size_t)M.B, hh = (size_t)M.h;
-    const size_t sizes[] = {G * M.wpc * 4, G * 4, G * 4, G * 8, G * B * 8, G * B * 4, hh * B, hh * 4, hh * 8, hh * 4, hh,
+    const int cap_bits = spin_capacity_bits > M.bits ? spin_capacity_bits : M.bits;
+    const size_t wpc_cap = (size_t)((M.N * cap_bits + 31) / 32);
+    const size_t sizes[] = {G * wpc_cap * 4, G * 4, G * 4, G * 8, G * B * 8, G * B * 4, hh * B, hh * 4, hh * 8, hh * 4, hh,
                             G, G * 4, G * (B + 2 * rewl::kShadowPad) * 8, hh, (size_t)rewl::kTieLog * 16,
                             sizeof(Ctl)};
     size_t off = 0;

@@ -81,8 +81,10 @@ namespace host {
 
 // Checks the parameters, computes the window table and the sizes of the device
 // arrays (h->parts, h->dbytes) and plans the sweep.  lanes: lanes per walker of
-// the fast sweep (0 = from the walker count).  No device memory is touched.
-rewl_status prepare_instance(rewl_s *h, const rewl_params &p, int spin_bits, int lanes);
+// the fast sweep (0 = from the walker count).  spin_capacity_bits (0 = the
+// packing chosen): the configuration buffers are sized for this packing, so
+// that a batch can repack its spins in place.  No device memory is touched.
+rewl_status prepare_instance(rewl_s *h, const rewl_params &p, int spin_bits, int lanes, int spin_capacity_bits = 0);
 // Points h->S at the arrays of a region of h->dbytes bytes at `base`.
 void carve_instance(rewl_s *h, void *base);
 // Queues zeroing, the window table, ln f = 1 and the initial configurations.
