@@ -339,6 +339,33 @@ rewl_status rewl_batch_create(const rewl_params *jobs, int n, int spin_bits, rew
  * either way.  Errors: REWL_ERR_ARG for another lanes value. */
 rewl_status rewl_batch_create_ext(const rewl_params *jobs, int n, int spin_bits, int lanes, rewl_batch_t *out);
 
+/* Autotuner (no counterpart in the paper: it picks how the batch runs, not
+ * what it computes).  Times the batch's candidate configurations -- spin
+ * packing 4 or 8 bits (when spin_bits was 0 and every q <= 16), walkers as lane
+ * groups of 32 with 36, 72 or 110 KB of shared memory per sweep CTA (when
+ * lanes was 0 and the walkers fit) or as a thread each with 128 or 256
+ * threads per CTA -- each over `rounds` rounds (after one round that settles
+ * it), by CUDA events on the batch's stream and the WL proposals counted, and
+ * leaves the batch in the fastest one.  The rounds it runs are ordinary rounds
+ * of every instance (no configuration changes a result).  The choice is
+ * cached per batch signature (device, freedoms, every instance's q, L, h, m,
+ * K) for the process: with rounds <= 0 a cached choice is applied without
+ * timing (*from_cache = 1), else 2 rounds per candidate are timed.
+ * entries[0 .. *n_entries - 1] (may be NULL with max_entries = 0) receive the
+ * timed candidates.  Errors: REWL_ERR_ARG, REWL_ERR_NOMEM, REWL_ERR_CUDA. */
+typedef struct rewl_tune_entry {
+    int spin_bits;      /* 4 or 8 */
+    int lanes;          /* 32 (lane groups) or 1 (a thread per walker) */
+    int cta_kb;         /* lane groups: shared memory per sweep CTA (KB), else 0 */
+    int threads;        /* a thread per walker: threads per CTA, else 0 */
+    double flips_per_s; /* WL proposals per second measured */
+} rewl_tune_entry;
+rewl_status rewl_batch_autotune(rewl_batch_t b, int rounds, rewl_tune_entry *entries, int max_entries,
+                                int *n_entries, int *from_cache);
+/* The batch's current configuration (each pointer may be NULL; cta_kb is 0 for
+ * a thread per walker, threads 0 for lane groups). */
+rewl_status rewl_batch_config(rewl_batch_t b, int *spin_bits, int *lanes, int *cta_kb, int *threads);
+
 /* Run rounds of every unfinished instance until all have converged or
  * max_rounds rounds were queued (<= 0: no limit); synchronises.
  * *n_converged (may be NULL) = instances whose windows are all done. */

@@ -48,6 +48,11 @@ class PipeRates(C.Structure):
                 ("max_clock_mhz", C.c_double)]
 
 
+class TuneEntry(C.Structure):
+    _fields_ = [("spin_bits", C.c_int), ("lanes", C.c_int), ("cta_kb", C.c_int), ("threads", C.c_int),
+                ("flips_per_s", C.c_double)]
+
+
 class Stats(C.Structure):
     _fields_ = [("rounds", C.c_longlong), ("flips", C.c_longlong), ("accepted", C.c_longlong),
                 ("exch_tried", C.c_longlong), ("exch_accepted", C.c_longlong),
@@ -109,6 +114,10 @@ def load():
     L.rewl_batch_instance.argtypes = [H, i32, C.POINTER(H)]
     L.rewl_batch_info.argtypes = [H, C.POINTER(C.c_int), C.POINTER(C.c_longlong), C.POINTER(C.c_size_t)]
     L.rewl_batch_stats.argtypes = [H, C.POINTER(Stats)]
+    L.rewl_batch_autotune.argtypes = [H, i32, C.POINTER(TuneEntry), i32, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.rewl_batch_autotune.restype = st
+    L.rewl_batch_config.argtypes = [H] + [C.POINTER(C.c_int)] * 4
+    L.rewl_batch_config.restype = st
     for name in ("rewl_batch_create", "rewl_batch_create_ext", "rewl_batch_run", "rewl_batch_run_async", "rewl_batch_sync",
                  "rewl_batch_set_stream", "rewl_batch_instance", "rewl_batch_info", "rewl_batch_stats"):
         getattr(L, name).restype = st

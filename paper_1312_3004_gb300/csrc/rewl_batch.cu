@@ -8,6 +8,9 @@
 // launches).
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "rewl.h"
@@ -47,8 +50,13 @@ struct SweepClass {
     rewl::WalkerItem *d_walkers = nullptr;
 };
 // Batches of at least this many walkers in all run a thread per walker with its
-// state in global memory (enough walkers to fill the SMs without lane groups).
+// state in global memory (enough walkers to fill the SMs without lane groups),
+// until rewl_batch_autotune measures otherwise.
 constexpr long long kWalkerModeMin = 16384;
+
+// Configurations the autotuner chose, by batch signature (process-wide).
+std::mutex g_tune_mu;
+std::map<std::string, Config> g_tune_cache;
 
 }  // namespace
 
@@ -374,6 +382,117 @@ rewl_status rewl_batch_create_ext(const rewl_params *jobs, int n, int spin_bits,
 }
 
 void rewl_batch_destroy(rewl_batch_t b) { destroy_batch(b); }
+
+rewl_status rewl_batch_autotune(rewl_batch_t b, int rounds, rewl_tune_entry *entries, int max_entries,
+                                int *n_entries, int *from_cache) {
+    REWL_API_TRY
+    const rewl::host::Range range("rewl_batch_autotune");
+    if (!b) return fail(REWL_ERR_ARG, "NULL batch");
+    if (max_entries < 0 || (max_entries > 0 && !entries)) return fail(REWL_ERR_ARG, "entries");
+    if (n_entries) *n_entries = 0;
+    if (from_cache) *from_cache = 0;
+    // the batch's signature: device, freedoms, and every instance's shape
+    std::string key = std::to_string(b->sms) + (b->bits_free ? "b" : "B") + (b->lanes_free ? "l" : "L") +
+                      std::to_string(b->cfg.bits) + "/" + std::to_string(b->cfg.lanes);
+    for (rewl_s *h : b->inst)
+        key += ";" + std::to_string(h->M.q) + "," + std::to_string(h->M.L) + "," + std::to_string(h->M.h) + "," +
+               std::to_string(h->M.m) + "," + std::to_string(h->M.K);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end() && rounds <= 0) {
+            if (from_cache) *from_cache = 1;
+            return configure(b, it->second);
+        }
+    }
+    if (rounds <= 0) rounds = 2;
+    std::vector<Config> cands;
+    const int bits_opts[2] = {b->cfg.bits, b->cfg.bits == 8 ? 4 : 8};
+    for (int bi = 0; bi < (b->bits_free ? 2 : 1); ++bi) {
+        const int bits = bits_opts[bi];
+        const int lane_opts[2] = {b->cfg.lanes, b->cfg.lanes == 32 ? 1 : 32};
+        for (int li = 0; li < (b->lanes_free ? 2 : 1); ++li) {
+            const int lanes = lane_opts[li];
+            if (lanes == 32 && !b->fits32[bits == 8]) continue;
+            Config c;
+            c.bits = bits;
+            c.lanes = lanes;
+            if (lanes == 32) {
+                for (int kb : {36, 72, 110}) {
+                    c.cta_kb = kb;
+                    cands.push_back(c);
+                }
+            } else {
+                for (int t : {128, 256}) {
+                    c.threads = t;
+                    cands.push_back(c);
+                }
+            }
+        }
+    }
+    cudaEvent_t e0, e1;
+    BATCH_CUDA(cudaEventCreate(&e0));
+    BATCH_CUDA(cudaEventCreate(&e1));
+    int best = -1, n_done = 0;
+    double best_rate = -1.0;
+    rewl_status st = REWL_OK;
+    int n_conv = 0;
+    for (size_t i = 0; i < cands.size() && st == REWL_OK; ++i) {
+        st = configure(b, cands[i]);
+        if (st) break;
+        st = enqueue_batch_rounds(b, 1);  // settles the new configuration
+        if (st == REWL_OK) st = read_batch_status(b, &n_conv);
+        if (st) break;
+        unsigned long long f0 = 0, f1 = 0;
+        for (size_t k = 0; k < b->inst.size(); ++k) f0 += b->h_ctls[k].flips;
+        cudaError_t e = cudaEventRecord(e0, b->stream);
+        if (e == cudaSuccess) st = enqueue_batch_rounds(b, rounds);
+        if (e == cudaSuccess && st == REWL_OK) e = cudaEventRecord(e1, b->stream);
+        if (e == cudaSuccess && st == REWL_OK) st = read_batch_status(b, &n_conv);
+        float ms = 0.0f;
+        if (e == cudaSuccess && st == REWL_OK) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess && st == REWL_OK) st = fail(REWL_ERR_CUDA, "autotune timing: %s", cudaGetErrorString(e));
+        if (st) break;
+        for (size_t k = 0; k < b->inst.size(); ++k) f1 += b->h_ctls[k].flips;
+        const double rate = ms > 0.0f ? (double)(f1 - f0) / (ms * 1e-3) : 0.0;
+        if (n_done < max_entries) {
+            rewl_tune_entry &en = entries[n_done];
+            en.spin_bits = cands[i].bits;
+            en.lanes = cands[i].lanes;
+            en.cta_kb = cands[i].lanes == 32 ? cands[i].cta_kb : 0;
+            en.threads = cands[i].lanes == 1 ? cands[i].threads : 0;
+            en.flips_per_s = rate;
+        }
+        ++n_done;
+        if (rate > best_rate) {
+            best_rate = rate;
+            best = (int)i;
+        }
+        if (n_conv == (int)b->inst.size()) break;  // nothing left to time
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) return st;
+    if (n_entries) *n_entries = std::min(n_done, max_entries);
+    if (best < 0) return REWL_OK;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache[key] = cands[(size_t)best];
+    }
+    return configure(b, cands[(size_t)best]);
+    REWL_API_CATCH
+}
+
+rewl_status rewl_batch_config(rewl_batch_t b, int *spin_bits, int *lanes, int *cta_kb, int *threads) {
+    REWL_API_TRY
+    if (!b) return fail(REWL_ERR_ARG, "NULL batch");
+    if (spin_bits) *spin_bits = b->cfg.bits;
+    if (lanes) *lanes = b->cfg.lanes;
+    if (cta_kb) *cta_kb = b->cfg.lanes == 32 ? b->cfg.cta_kb : 0;
+    if (threads) *threads = b->cfg.lanes == 1 ? b->cfg.threads : 0;
+    return REWL_OK;
+    REWL_API_CATCH
+}
 
 rewl_status rewl_batch_set_stream(rewl_batch_t b, void *stream) {
     REWL_API_TRY

@@ -247,6 +247,20 @@ class Batch:
         check(self._L.rewl_batch_sync(self._h, C.byref(n)))
         return n.value
 
+    def autotune(self, rounds=2):
+        """Time the batch's candidate configurations (rewl_batch_autotune) and
+        keep the fastest: (list of timed candidates as dicts, from_cache)."""
+        ent = (_lib.TuneEntry * 16)()
+        n, cached = C.c_int(0), C.c_int(0)
+        check(self._L.rewl_batch_autotune(self._h, rounds, ent, 16, C.byref(n), C.byref(cached)))
+        return [{k: getattr(ent[i], k) for k, _ in _lib.TuneEntry._fields_} for i in range(n.value)], bool(cached.value)
+
+    def config(self):
+        """The batch's configuration: spin bits, lanes, CTA shared memory (KB) or threads per CTA."""
+        v = [C.c_int(0) for _ in range(4)]
+        check(self._L.rewl_batch_config(self._h, *[C.byref(x) for x in v]))
+        return dict(zip(("spin_bits", "lanes", "cta_kb", "threads"), (x.value for x in v)))
+
     def instance(self, i):
         """Read-only REWL handle of instance i (owned by the batch)."""
         if i not in self._views:

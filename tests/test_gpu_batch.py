@@ -122,3 +122,32 @@ def test_full_batched_workload_sampled_instances_match_the_oracle():
         assert np.array_equal(v.get("hist"), orc.H()), i
         assert np.array_equal(v.get("replica"), orc.rep()), i
         assert np.array_equal(v.get("trips"), orc.rt_trips()), i
+
+
+def test_autotuner_changes_no_result_and_caches_its_choice():
+    """The autotuner runs ordinary rounds in every candidate configuration
+    (spin packing 4 / 8 bits, lane groups with three CTA sizes, a thread per
+    walker with two CTA sizes), repacking the spins in place between them; the
+    instances must still equal their runs alone, and a second batch of the
+    same jobs takes the cached choice without timing."""
+    jobs = jobs_mixed()
+    assert all(j["q"] <= 16 for j in jobs)  # packing free to change
+    b = Batch(jobs)
+    b.run(2)
+    timed, cached = b.autotune(1)
+    assert not cached and len(timed) >= 4
+    assert {t["spin_bits"] for t in timed} == {4, 8} and {t["lanes"] for t in timed} == {1, 32}
+    assert all(t["flips_per_s"] > 0 for t in timed)
+    best = max(timed, key=lambda t: t["flips_per_s"])
+    cfg = b.config()
+    assert (cfg["spin_bits"], cfg["lanes"]) == (best["spin_bits"], best["lanes"])
+    rounds = b.stats()["rounds"]
+    b.run(3)
+    for i, j in enumerate(jobs):
+        a = alone(j, rounds + 3)
+        v = b.instance(i)
+        for f in FIELDS:
+            assert np.array_equal(v.get(f), a.get(f)), (i, f)
+    b2 = Batch(jobs)
+    timed2, cached2 = b2.autotune(0)
+    assert cached2 and timed2 == [] and b2.config() == cfg
