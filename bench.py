@@ -64,7 +64,7 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="potts10_L80",
                     help="potts10_L80 (default), potts10_L300 (the paper's size), potts10_L20, ising_L8, "
-                         "batched2048 or serving")
+                         "batched2048, serving (small jobs) or serving_full (the stated sizes, cost-capped)")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--schedule", default="halving", choices=["halving", "inv_t"],
@@ -72,6 +72,8 @@ def parse_args():
                          "two, so every WL step takes the binary64 add)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--jobs", type=int, default=100, help="arrivals of the serving trace")
+    ap.add_argument("--cost-cap", type=float, default=1e10,
+                    help="serving_full: jobs whose estimated cost exceeds this many proposals are left out")
     ap.add_argument("--converge", default="",
                     help="comma-separated seeds: time each run to ln f < ln f_final instead of timing rounds")
     ap.add_argument("--converge-limit", type=float, default=1800.0, help="seconds per seed before giving up")
@@ -598,6 +600,98 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serving_full(args):
+    """The serving workload at its stated sizes: the first --jobs arrivals of a
+    Poisson stream (50/s) of jobs with q 2..10, L 16..96, h 8..64, m 2..8,
+    ln f_final 1e-6 / 1e-8.  Calibration first: every job's cost is estimated
+    (workloads.job_cost_estimate) and the offered load (estimated proposals per
+    second of trace) is set against the server's measured capacity.  The full
+    stream offers about a thousand times the capacity of one GPU, so it is
+    trimmed by a cost cap (--cost-cap proposals): the jobs under the cap are
+    served by continuous batching at their own arrival times, the others are
+    left out and counted.  Plain form: each served job alone, one at a time in
+    arrival order; its solo time is its own proposal count (the same alone as
+    in the mix) over its solo rate, measured on the job alone over its first
+    rounds (which overstates the solo rate late in a run: the plain latencies
+    are a lower bound)."""
+    import numpy as np
+    import torch
+
+    from paper_1312_3004_gb300 import REWL, Server
+    from paper_1312_3004_gb300 import workloads as WL
+
+    full = WL.serving_trace_full(n=args.jobs)
+    span = full[-1][0]
+    costs = [WL.job_cost_estimate(p) for _, p in full]
+    kept = [(t, p, c) for (t, p), c in zip(full, costs) if c <= args.cost_cap]
+    srv = Server(pool_bytes=8 << 30, max_jobs=1024)
+    ids = []
+    t0 = time.perf_counter()
+    k = 0
+    busy_flips, busy_s = 0, 0.0
+    while True:
+        now = time.perf_counter() - t0
+        while k < len(kept) and kept[k][0] <= now:
+            ids.append((srv.submit(**kept[k][1]), kept[k][0], kept[k][2]))
+            k += 1
+        f_before = srv.info()["flips"]
+        a = time.perf_counter()
+        running, queued = srv.step(rounds=4)
+        if running:
+            busy_s += time.perf_counter() - a
+            busy_flips += srv.info()["flips"] - f_before
+        if k == len(kept) and running == 0 and queued == 0:
+            break
+        if running == 0 and queued == 0 and k < len(kept):
+            time.sleep(max(0.0, min(0.01, kept[k][0] - (time.perf_counter() - t0))))
+    wall = time.perf_counter() - t0
+    lat, jflips = [], []
+    for jid, arrival, _ in ids:
+        info = srv.job_info(jid)
+        lat.append(info["t_done"] - (t0 + arrival) if info["t_done"] > 0 else float("nan"))
+        jflips.append(info["flips"])
+    lat = np.array(lat)
+    capacity = busy_flips / max(busy_s, 1e-9)
+    # plain: each job alone, one at a time in arrival order
+    solo = []
+    stream = torch.cuda.Stream()
+    for (_, p, _), fl in zip(kept, jflips):
+        r = REWL(*WL.rewl_args(p, p["seed"]), stream=stream)
+        r.run(1)
+        f0 = r.stats()["flips"]
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        r.run(4)
+        dt = time.perf_counter() - a
+        rate = (r.stats()["flips"] - f0) / dt if dt > 0 else float("inf")
+        solo.append(fl / rate)
+        r.close()
+    finish, plat = 0.0, []
+    for (arrival, _, _), d in zip(kept, solo):
+        finish = max(finish, arrival) + d
+        plat.append(finish - arrival)
+    plat = np.array(plat)
+    line = {"metric": "request latency p50/p99", "value": float(np.percentile(lat, 99)), "unit": "s (p99)",
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "throughput_flips_per_s": srv.info()["flips"] / wall, "n_gpus": 1, "higher_is_better": False,
+            "data": "synthetic", "wall_s": wall,
+            "config": {"workload": "serving_full", "arrivals": len(full), "arrival_rate_per_s": 50.0,
+                       "trace": "Poisson 50/s, q 2..10, L 16..96, h 8..64, m 2..8, ln f_final 1e-6/1e-8, K 10^4"},
+            "calibration": {"offered_flips_per_s_full": float(sum(costs) / span),
+                            "capacity_flips_per_s": capacity,
+                            "offered_over_capacity_full": float(sum(costs) / span / capacity),
+                            "cost_cap_proposals": args.cost_cap, "served_jobs": len(kept),
+                            "left_out_jobs": len(full) - len(kept),
+                            "offered_flips_per_s_served": float(sum(c for _, _, c in kept) / span),
+                            "measured_over_estimated_cost": float(sum(jflips) / max(1.0, sum(c for _, _, c in kept))),
+                            "cost_model": "workloads.job_cost_estimate"},
+            "plain": {"p50_s": float(np.percentile(plat, 50)), "p99_s": float(np.percentile(plat, 99)),
+                      "form": "each served job alone, one at a time, first-come first-served (solo time = its "
+                              "proposals / its solo rate over its first rounds: a lower bound)",
+                      "busy_s": float(sum(solo))}}
+    print(json.dumps(line), flush=True)
+
+
 def analyse(r, p):
     """Canonical analysis of a converged run's joined ln g through the
     library: the specific-heat maximum and the equal-peak temperature Tc(L)
@@ -745,6 +839,8 @@ def main():
         run_batched(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.workload == "serving_full":
+        run_serving_full(args)
     else:
         run_ours(args)
 

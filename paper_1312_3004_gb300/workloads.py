@@ -4,6 +4,8 @@ The paper's Potts runs (Sec. 3.1) are defined by lattice parameters and seeds;
 there is no dataset.  These named configurations are shared by the tests, the
 benchmark and the CPU baseline.
 """
+import math
+
 import numpy as np
 
 # Each entry: q, L, h, overlap, m, lnf_final, flatness, exchange_interval, spin_bits
@@ -72,3 +74,35 @@ def serving_trace(n=100, rate=50.0, master_seed=0x5EED0005):
                             lnf_final=float(rng.choice([1e-4, 1e-5])), flatness=0.8,
                             exchange_interval=2000, seed=int(rng.integers(1, 2**63)))))
     return out
+
+
+def serving_trace_full(n=1000, rate=50.0, master_seed=0x5EED0005):
+    """Poisson arrivals (exponential gaps, mean 1/rate s) of density-of-states
+    jobs at the serving workload's stated sizes: q in {2..10}, L in {16..96},
+    h in {8..64}, m in {2..8}, ln f_final in {1e-6, 1e-8}, 10^4 steps between
+    exchanges, overlap 0.75, flatness 0.8.  Returns [(arrival_s, params)]."""
+    rng = np.random.default_rng(master_seed)
+    t = 0.0
+    out = []
+    for _ in range(n):
+        t += float(rng.exponential(1.0 / rate))
+        out.append((t, dict(q=int(rng.integers(2, 11)), L=int(rng.integers(16, 97)), h=int(rng.integers(8, 65)),
+                            overlap=0.75, m=int(rng.integers(2, 9)),
+                            lnf_final=float(rng.choice([1e-6, 1e-8])), flatness=0.8,
+                            exchange_interval=10_000, seed=int(rng.integers(1, 2**63)))))
+    return out
+
+
+def job_cost_estimate(p):
+    """Estimated WL proposals for a job to converge: walkers x steps per
+    walker, with steps per walker = 1.9e7 (W / 47)^1.83 x (iterations / 27),
+    W the bins per window and iterations = ceil(log2(1 / ln f_final)) + 1 --
+    a fit to converged runs of q = 10, h = 8, m = 4 at L = 8, 12, 16, 20 and
+    ln f_final = 1e-8 (W = 47 .. 291; 1.9e7 .. 5.3e8 steps per walker).  Used
+    only to calibrate the offered load of a serving trace and to cap it; large
+    lattices near a first-order transition take longer than it says."""
+    N = p["L"] * p["L"]
+    R = 2 * N
+    W = min(R, math.ceil(R / (1.0 + (p["h"] - 1) * (1.0 - p["overlap"]))))
+    iters = math.ceil(math.log2(1.0 / p["lnf_final"])) + 1
+    return p["h"] * p["m"] * 1.9e7 * (W / 47.0) ** 1.83 * iters / 27.0

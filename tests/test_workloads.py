@@ -38,3 +38,35 @@ def test_serving_trace_is_a_poisson_stream():
     assert abs(gaps.std() / gaps.mean() - 1.0) < 0.1  # exponential: coefficient of variation 1
     for _, j in tr[:200]:
         assert 2 <= j["q"] <= 10 and 6 <= j["L"] <= 12 and 2 <= j["h"] <= 6 and 2 <= j["m"] <= 4
+
+
+def test_full_serving_trace_has_the_stated_sizes():
+    tr = WL.serving_trace_full(n=1000)
+    assert tr == WL.serving_trace_full(n=1000)
+    t = np.array([x[0] for x in tr])
+    gaps = np.diff(np.concatenate([[0.0], t]))
+    assert abs(gaps.mean() - 1 / 50.0) < 0.002
+    js = [j for _, j in tr]
+    assert {j["q"] for j in js} == set(range(2, 11))
+    assert min(j["L"] for j in js) >= 16 and max(j["L"] for j in js) <= 96
+    assert min(j["h"] for j in js) >= 8 and max(j["h"] for j in js) <= 64
+    assert {j["m"] for j in js} == set(range(2, 9))
+    assert {j["lnf_final"] for j in js} == {1e-6, 1e-8}
+    assert all(j["exchange_interval"] == 10_000 for j in js)
+
+
+def test_job_cost_estimate_reproduces_its_calibration_runs():
+    """The cost model against the converged oracle runs it was fitted to
+    (tests/golden/potts10_L{8,12,16,20}_converged.json: median WL steps of
+    8 windows x 4 walkers), within a factor 1.3."""
+    import json
+    import os
+    import statistics
+
+    here = os.path.join(os.path.dirname(__file__), "golden")
+    for L in (8, 12, 16, 20):
+        with open(os.path.join(here, "potts10_L%d_converged.json" % L)) as f:
+            runs = json.load(f)["runs"]
+        measured = statistics.median(r["wl_steps"] for r in runs)
+        est = WL.job_cost_estimate(WL.params("potts10_L%d" % L))
+        assert 1 / 1.3 < est / measured < 1.3, (L, est, measured)
