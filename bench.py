@@ -141,6 +141,67 @@ def summarize_clocks(lines, uuid=None, t0=None, t1=None):
             "reasons": reasons, "samples": len(rows)}
 
 
+class NvmlSampler:
+    """SM clock and clock-event reasons read through NVML (the driver's
+    libnvidia-ml, by ctypes) every 2 ms from a thread during the timed region:
+    a timed region of a few tens of milliseconds still gets a dozen samples.
+    Reading only; nothing is set."""
+
+    # nvmlClocksEventReason bits
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, uuid):
+        import ctypes as C
+        import threading
+
+        self.C, self.threading = C, threading
+        self.lib = C.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.h = C.c_void_p()
+        if not uuid or self.lib.nvmlDeviceGetHandleByUUID(str(uuid).encode(), C.byref(self.h)) != 0:
+            raise OSError("no NVML handle for %s" % uuid)
+        mx = C.c_uint(0)
+        self.lib.nvmlDeviceGetMaxClockInfo(self.h, 1, C.byref(mx))  # 1 = NVML_CLOCK_SM
+        self.max_mhz = float(mx.value)
+        fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None)
+        self.reasons_fn = fn if fn is not None else self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        self.samples, self.stop_flag, self.thread = [], False, None
+
+    def _run(self):
+        C = self.C
+        clk, rs = C.c_uint(0), C.c_ulonglong(0)
+        while not self.stop_flag:
+            t = time.time()
+            if self.lib.nvmlDeviceGetClockInfo(self.h, 1, C.byref(clk)) == 0:
+                r = rs.value if self.reasons_fn(self.h, C.byref(rs)) == 0 else 0
+                self.samples.append((t, float(clk.value), int(r)))
+            time.sleep(0.002)
+
+    def start(self):
+        self.thread = self.threading.Thread(target=self._run, daemon=True)
+        self.thread.start()
+
+    def stop(self, t0=None, t1=None):
+        self.stop_flag = True
+        self.thread.join()
+        rows = [x for x in self.samples if t0 is None or t1 is None or t0 <= x[0] <= t1] or self.samples
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["no samples"], "source": "nvml"}
+        reasons = sorted({name for _, _, r in rows for bit, name in self.REASONS.items() if r & bit})
+        return {"sm_mhz": statistics.median(x[1] for x in rows), "sm_min_mhz": min(x[1] for x in rows),
+                "sm_max_mhz": self.max_mhz, "reasons": reasons, "samples": len(rows), "source": "nvml, every 2 ms"}
+
+
+def clock_sampler(uuid):
+    """NVML sampling when the driver library answers, else nvidia-smi's."""
+    try:
+        return NvmlSampler(uuid)
+    except Exception:
+        return ClockSampler(uuid)
+
+
 class ClockSampler:
     """nvidia-smi samples every 100 ms around the timed region."""
 
@@ -316,7 +377,7 @@ def run_ours(args):
     props = torch.cuda.get_device_properties(local)
     uuid = getattr(props, "uuid", None)
     uuid = ("GPU-" + str(uuid)) if uuid is not None and not str(uuid).startswith("GPU-") else uuid
-    sampler = ClockSampler(uuid if uuid else None)
+    sampler = clock_sampler(uuid if uuid else None)
     events = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(args.steps)]
     s0 = r.stats()
     if dist:
@@ -484,7 +545,10 @@ def run_batched(args):
     f0 = b.stats()["flips"]
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     torch.cuda.synchronize()
-    sampler = ClockSampler(None)
+    props = torch.cuda.get_device_properties(0)
+    uuid = getattr(props, "uuid", None)
+    uuid = ("GPU-" + str(uuid)) if uuid is not None and not str(uuid).startswith("GPU-") else uuid
+    sampler = clock_sampler(uuid)
     sampler.start()
     time.sleep(0.3)
     epoch0 = time.time()
