@@ -362,6 +362,16 @@ typedef struct rewl_tune_entry {
 } rewl_tune_entry;
 rewl_status rewl_batch_autotune(rewl_batch_t b, int rounds, rewl_tune_entry *entries, int max_entries,
                                 int *n_entries, int *from_cache);
+/* The same for one handle (no counterpart in the paper): the fast sweep's lanes
+ * per walker (32, 16, 8, 4, 2, 1; the lattice placed by the size rule) are
+ * each timed over `rounds` rounds (<= 0: 2) after one settling round, and the
+ * fastest is kept (REWL_OPT_LANES).  The rounds are ordinary rounds of the run:
+ * the handle advances by (1 + rounds) rounds per candidate, and no choice
+ * changes a result.  entries receive the timed candidates (spin_bits, lanes,
+ * cta_kb = shared memory per CTA in KB, threads per CTA, flips_per_s).  Stops
+ * early once the run has converged.  Errors: REWL_ERR_ARG, REWL_ERR_STATE
+ * (instance of a batch, or in production), REWL_ERR_CUDA. */
+rewl_status rewl_autotune(rewl_t h, int rounds, rewl_tune_entry *entries, int max_entries, int *n_entries);
 /* The batch's current configuration (each pointer may be NULL; cta_kb is 0 for
  * a thread per walker, threads 0 for lane groups). */
 rewl_status rewl_batch_config(rewl_batch_t b, int *spin_bits, int *lanes, int *cta_kb, int *threads);

@@ -116,6 +116,8 @@ def load():
     L.rewl_batch_stats.argtypes = [H, C.POINTER(Stats)]
     L.rewl_batch_autotune.argtypes = [H, i32, C.POINTER(TuneEntry), i32, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.rewl_batch_autotune.restype = st
+    L.rewl_autotune.argtypes = [H, i32, C.POINTER(TuneEntry), i32, C.POINTER(C.c_int)]
+    L.rewl_autotune.restype = st
     L.rewl_batch_config.argtypes = [H] + [C.POINTER(C.c_int)] * 4
     L.rewl_batch_config.restype = st
     for name in ("rewl_batch_create", "rewl_batch_create_ext", "rewl_batch_run", "rewl_batch_run_async", "rewl_batch_sync",

@@ -1,6 +1,7 @@
 // rewl_host.cu -- host driver behind include/rewl.h: parameter checks, the
 // window table, device state, the round loop as a CUDA graph, state access,
 // joining of the windows' pieces (Sec. 2, Fig. 2) and save / load.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -531,6 +532,64 @@ rewl_status rewl_set_option(rewl_t h, int option, long long value) {
         h->graph = nullptr;
     }
     return build_graph(h);
+    REWL_API_CATCH
+}
+
+rewl_status rewl_autotune(rewl_t h, int rounds, rewl_tune_entry *entries, int max_entries, int *n_entries) {
+    REWL_API_TRY
+    const rewl::host::Range range("rewl_autotune");
+    if (h && !h->owns) return fail(REWL_ERR_STATE, "this instance belongs to a batch: tune the batch");
+    if (!h) return fail(REWL_ERR_ARG, "NULL handle");
+    if (h->M.production) return fail(REWL_ERR_STATE, "in production: options are fixed");
+    if (max_entries < 0 || (max_entries > 0 && !entries)) return fail(REWL_ERR_ARG, "entries");
+    if (rounds <= 0) rounds = 2;
+    if (n_entries) *n_entries = 0;
+    if (h->plan.kind != rewl::SWEEP_FAST) return REWL_OK;  // the reference sweep has nothing to tune
+    cudaEvent_t e0, e1;
+    REWL_CUDA(cudaEventCreate(&e0));
+    REWL_CUDA(cudaEventCreate(&e1));
+    int best = 0, n_done = 0;
+    double best_rate = -1.0;
+    rewl_status st = REWL_OK;
+    for (int lanes : {32, 16, 8, 4, 2, 1}) {
+        st = rewl_set_option(h, REWL_OPT_LANES, lanes);
+        if (st == REWL_ERR_ARG) {  // does not fit in shared memory: not a candidate
+            st = REWL_OK;
+            continue;
+        }
+        if (st) break;
+        st = enqueue_rounds(h, 1);  // settles the new plan
+        if (st == REWL_OK) st = read_ctl(h);
+        if (st || h->h_ctl->all_done) break;
+        const unsigned long long f0 = h->h_ctl->flips;
+        cudaError_t e = cudaEventRecord(e0, h->stream);
+        if (e == cudaSuccess) st = enqueue_rounds(h, rounds);
+        if (e == cudaSuccess && st == REWL_OK) e = cudaEventRecord(e1, h->stream);
+        if (e == cudaSuccess && st == REWL_OK) st = read_ctl(h);
+        float ms = 0.0f;
+        if (e == cudaSuccess && st == REWL_OK) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess && st == REWL_OK) st = fail(REWL_ERR_CUDA, "autotune timing: %s", cudaGetErrorString(e));
+        if (st) break;
+        const double rate = ms > 0.0f ? (double)(h->h_ctl->flips - f0) / (ms * 1e-3) : 0.0;
+        if (n_done < max_entries) {
+            rewl_tune_entry &en = entries[n_done];
+            en.spin_bits = h->M.bits;
+            en.lanes = lanes;
+            en.cta_kb = (int)(h->plan.smem / 1024);
+            en.threads = h->plan.threads;
+            en.flips_per_s = rate;
+        }
+        ++n_done;
+        if (rate > best_rate) {
+            best_rate = rate;
+            best = lanes;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) return st;
+    if (n_entries) *n_entries = std::min(n_done, max_entries);
+    return best_rate >= 0.0 ? rewl_set_option(h, REWL_OPT_LANES, best) : REWL_OK;
     REWL_API_CATCH
 }
 

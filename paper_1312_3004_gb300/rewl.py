@@ -164,6 +164,14 @@ class REWL:
     def round(self):
         return int(self.get("round")[0])
 
+    def autotune(self, rounds=2):
+        """Time the fast sweep's lane widths on the next rounds (rewl_autotune)
+        and keep the fastest; returns the timed candidates."""
+        ent = (_lib.TuneEntry * 8)()
+        n = C.c_int(0)
+        check(self._L.rewl_autotune(self._h, rounds, ent, 8, C.byref(n)))
+        return [{k: getattr(ent[i], k) for k, _ in _lib.TuneEntry._fields_} for i in range(n.value)]
+
     def production_start(self, n_obins):
         """Fixed weights 1/g(E) from the current ln g (ln f = 0) and a histogram
         H(E, O) of the majority count in n_obins classes (Sec. 3.2)."""

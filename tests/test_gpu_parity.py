@@ -374,3 +374,20 @@ def test_a_planted_exchange_near_tie_is_logged():
         o2.invert_decision(1, 0, 0)
         o2.exchange()
         assert np.array_equal(got, o2.rep())
+
+
+@pytest.mark.parametrize("case", [SMALL[0], SMALL[2], SMALL[6]])
+def test_autotune_changes_no_result(case):
+    """rewl_autotune times every lane width on ordinary rounds and keeps the
+    fastest: the state afterwards is the oracle's after as many rounds."""
+    from paper_1312_3004_gb300 import _lib
+    *args, sb = case
+    gpu, orc = make_pair(*args, spin_bits=sb)
+    gpu.run(2)
+    timed = gpu.autotune(1)
+    assert len(timed) >= 1 and all(t["flips_per_s"] > 0 for t in timed)
+    best = max(timed, key=lambda t: t["flips_per_s"])
+    assert gpu.get_option(_lib.OPT_LANES) == best["lanes"]
+    gpu.run(3)
+    orc.run(gpu.round)
+    assert_parity(gpu, orc)
