@@ -77,6 +77,10 @@ def parse_args():
     ap.add_argument("--converge", default="",
                     help="comma-separated seeds: time each run to ln f < ln f_final instead of timing rounds")
     ap.add_argument("--converge-limit", type=float, default=1800.0, help="seconds per seed before giving up")
+    ap.add_argument("--converge-save", default="",
+                    help="with --concurrent: save each unfinished seed's state and seconds here at the end")
+    ap.add_argument("--converge-resume", default="",
+                    help="with --concurrent: continue the seeds saved here (their seconds are added)")
     ap.add_argument("--ref-chunk", type=int, default=32,
                     help="--impl reference: walkers advanced by K WL steps in one timed step")
     ap.add_argument("--concurrent", action="store_true",
@@ -829,13 +833,34 @@ def run_converge(args):
     sampler.start()
     epoch0 = time.time()
     if args.concurrent:
-        hs = [(seed, REWL(*WL.rewl_args(p, seed), spin_bits=p["spin_bits"], stream=torch.cuda.Stream()))
-              for seed in seeds]
+        # A run longer than one job of the machine is run in segments: the state of
+        # every unfinished seed is saved (rewl_save) with the seconds it has run,
+        # and the next segment loads it (rewl_load) and adds those seconds -- the
+        # resumed run is the same run, step for step.
+        prior, done_before, traces = {}, {}, {}
+        for seed in seeds:
+            meta = os.path.join(args.converge_resume, "seed%d.json" % seed) if args.converge_resume else None
+            if meta and os.path.exists(meta):
+                with open(meta) as f:
+                    m = json.load(f)
+                prior[seed] = m["seconds"]
+                traces[seed] = m["progress"]
+                if m["converged"]:
+                    done_before[seed] = m
+        hs = []
+        for seed in seeds:
+            if seed in done_before:
+                continue
+            r = REWL(*WL.rewl_args(p, seed), spin_bits=p["spin_bits"], stream=torch.cuda.Stream())
+            if seed in prior:
+                with open(os.path.join(args.converge_resume, "seed%d.blob" % seed), "rb") as f:
+                    r.load(f.read())
+            hs.append((seed, r))
+            traces.setdefault(seed, [])
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         finish = {}
         el, last = 0.0, 0.0
-        traces = {seed: [] for seed, _ in hs}
         while len(finish) < len(hs) and el < args.converge_limit:
             for seed, r in hs:
                 if seed not in finish:
@@ -849,18 +874,29 @@ def run_converge(args):
                 last = el
                 for seed, r in hs:
                     st = r.stats()
-                    traces[seed].append([round(el, 1), st["windows_done"], st["max_lnf"]])
-                print(json.dumps({"progress_s": round(el, 1), "seeds": {str(k): v[-1][1:] for k, v in traces.items()}}),
-                      flush=True)
+                    traces[seed].append([round(prior.get(seed, 0.0) + el, 1), st["windows_done"], st["max_lnf"]])
+                print(json.dumps({"progress_s": round(el, 1), "seeds": {str(k): v[-1][1:] for k, v in traces.items()
+                                                                         if v}}), flush=True)
+        for seed, m in done_before.items():
+            runs.append(m)
         for seed, r in hs:
             s = r.stats()
-            secs = finish.get(seed, el)
+            secs = prior.get(seed, 0.0) + finish.get(seed, el)
+            if args.converge_save and seed not in finish:
+                os.makedirs(args.converge_save, exist_ok=True)
+                with open(os.path.join(args.converge_save, "seed%d.blob" % seed), "wb") as f:
+                    f.write(r.save())
             runs.append({"seed": seed, "converged": seed in finish, "seconds": secs, "rounds": s["rounds"],
                          "flips": s["flips"], "mean_flips_per_s": s["flips"] / secs,
                          "windows_done": s["windows_done"], "progress": traces[seed],
                          "analysis": analyse(r, p) if seed in finish else None})
             runs[-1]["oracle"] = oracle_reference(args.workload, seed, runs[-1]["analysis"],
                                                   r.lng() if seed in finish else None)
+            runs[-1]["segments"] = (1 + (1 if seed in prior else 0))
+            if args.converge_save:
+                os.makedirs(args.converge_save, exist_ok=True)
+                with open(os.path.join(args.converge_save, "seed%d.json" % seed), "w") as f:
+                    json.dump(runs[-1], f)
             r.close()
     for seed in ([] if args.concurrent else seeds):
         r = REWL(*WL.rewl_args(p, seed), spin_bits=p["spin_bits"])
