@@ -853,8 +853,10 @@ def run_converge(args):
                 continue
             r = REWL(*WL.rewl_args(p, seed), spin_bits=p["spin_bits"], stream=torch.cuda.Stream())
             if seed in prior:
+                import zlib
+
                 with open(os.path.join(args.converge_resume, "seed%d.blob" % seed), "rb") as f:
-                    r.load(f.read())
+                    r.load(zlib.decompress(f.read()))
             hs.append((seed, r))
             traces.setdefault(seed, [])
         torch.cuda.synchronize()
@@ -884,8 +886,10 @@ def run_converge(args):
             secs = prior.get(seed, 0.0) + finish.get(seed, el)
             if args.converge_save and seed not in finish:
                 os.makedirs(args.converge_save, exist_ok=True)
+                import zlib
+
                 with open(os.path.join(args.converge_save, "seed%d.blob" % seed), "wb") as f:
-                    f.write(r.save())
+                    f.write(zlib.compress(r.save(), 1))
             runs.append({"seed": seed, "converged": seed in finish, "seconds": secs, "rounds": s["rounds"],
                          "flips": s["flips"], "mean_flips_per_s": s["flips"] / secs,
                          "windows_done": s["windows_done"], "progress": traces[seed],

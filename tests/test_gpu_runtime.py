@@ -55,7 +55,7 @@ def test_caching_allocator_of_torch_supplies_the_state():
         bt = Batch([SMALL_JOB, dict(SMALL_JOB, seed=2)])
     finally:
         R.set_allocator()
-    assert len(live) == 2
+    assert len(live) == 3  # the handle's state; the batch's state and its configuration tables
     b = REWL(*ARGS)
     a.run(5)
     b.run(5)
