@@ -53,7 +53,7 @@ LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 # DRAM bytes (read + write) of one sweep launch, from ncu captures of the
 # current kernels (profiles/sweep_fast_potts10_L80.md, profiles/batch_walker_batched2048.md)
-TRAFFIC_PER_LAUNCH = {"potts10_L80": 10.19e6, "batched2048": 6.40e9}
+TRAFFIC_PER_LAUNCH = {"potts10_L80": 10.12e6, "batched2048": 6.40e9}
 
 
 def parse_args():
@@ -692,6 +692,17 @@ def run_serving_full(args):
     span = full[-1][0]
     costs = [WL.job_cost_estimate(p) for _, p in full]
     kept = [(t, p, c) for (t, p), c in zip(full, costs) if c <= args.cost_cap]
+    # capacity at full load: every served job resident at once, ~10 s of rounds
+    cal = Server(pool_bytes=8 << 30, max_jobs=1024)
+    for _, p, _ in kept:
+        cal.submit(**p)
+    cal.step(rounds=1)
+    f0 = cal.info()["flips"]
+    a = time.perf_counter()
+    while time.perf_counter() - a < 10.0:
+        cal.step(rounds=4)
+    capacity_full = (cal.info()["flips"] - f0) / (time.perf_counter() - a)
+    cal.close()
     srv = Server(pool_bytes=8 << 30, max_jobs=1024)
     ids = []
     t0 = time.perf_counter()
@@ -719,7 +730,7 @@ def run_serving_full(args):
         lat.append(info["t_done"] - (t0 + arrival) if info["t_done"] > 0 else float("nan"))
         jflips.append(info["flips"])
     lat = np.array(lat)
-    capacity = busy_flips / max(busy_s, 1e-9)
+    busy_rate = busy_flips / max(busy_s, 1e-9)
     # plain: each job alone, one at a time in arrival order
     solo = []
     stream = torch.cuda.Stream()
@@ -746,8 +757,10 @@ def run_serving_full(args):
             "config": {"workload": "serving_full", "arrivals": len(full), "arrival_rate_per_s": 50.0,
                        "trace": "Poisson 50/s, q 2..10, L 16..96, h 8..64, m 2..8, ln f_final 1e-6/1e-8, K 10^4"},
             "calibration": {"offered_flips_per_s_full": float(sum(costs) / span),
-                            "capacity_flips_per_s": capacity,
-                            "offered_over_capacity_full": float(sum(costs) / span / capacity),
+                            "capacity_flips_per_s": capacity_full,
+                            "capacity_how": "every served job resident at once, 10 s of rounds",
+                            "mean_rate_while_busy": busy_rate,
+                            "offered_over_capacity_full": float(sum(costs) / span / capacity_full),
                             "cost_cap_proposals": args.cost_cap, "served_jobs": len(kept),
                             "left_out_jobs": len(full) - len(kept),
                             "offered_flips_per_s_served": float(sum(c for _, _, c in kept) / span),

@@ -423,8 +423,16 @@ rewl_status rewl_server_create(size_t pool_bytes, int max_jobs, rewl_server_t *o
  * Errors: REWL_ERR_ARG (parameters), REWL_ERR_NOMEM (larger than the pool). */
 rewl_status rewl_server_submit(rewl_server_t s, const rewl_params *params, int spin_bits, long long *job_id);
 /* Admit, advance every resident job by rounds (>= 1) rounds, retire; then
- * *n_running / *n_queued (may be NULL) count resident and waiting jobs. */
+ * *n_running / *n_queued (may be NULL) count resident and waiting jobs.
+ * The resident walkers run as lane groups of 32 (state staged in shared
+ * memory) or a thread each (state in global memory): from 512 resident walkers
+ * on, whenever their number has changed by half since the last choice, the
+ * first two rounds of a step time one mapping each (CUDA events) and the faster
+ * is kept (no counterpart in the paper; both compute the same states). */
 rewl_status rewl_server_step(rewl_server_t s, long long rounds, int *n_running, int *n_queued);
+/* The current mapping (*lanes = 32 or 1) and the resident walker count it was
+ * chosen at (0: not timed, fewer than 512 walkers).  Each pointer may be NULL. */
+rewl_status rewl_server_mapping(rewl_server_t s, int *lanes, long long *tuned_walkers);
 /* *state = REWL_JOB_*. */
 rewl_status rewl_server_poll(rewl_server_t s, long long job_id, int *state);
 /* Joined, normalised ln g of a finished job into `out` (host, 2N + 1 doubles,

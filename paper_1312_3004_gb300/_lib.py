@@ -116,6 +116,8 @@ def load():
     L.rewl_batch_stats.argtypes = [H, C.POINTER(Stats)]
     L.rewl_batch_autotune.argtypes = [H, i32, C.POINTER(TuneEntry), i32, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.rewl_batch_autotune.restype = st
+    L.rewl_server_mapping.argtypes = [H, C.POINTER(C.c_int), C.POINTER(C.c_longlong)]
+    L.rewl_server_mapping.restype = st
     L.rewl_autotune.argtypes = [H, i32, C.POINTER(TuneEntry), i32, C.POINTER(C.c_int)]
     L.rewl_autotune.restype = st
     L.rewl_batch_config.argtypes = [H] + [C.POINTER(C.c_int)] * 4

@@ -34,6 +34,9 @@ namespace {
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+constexpr int kWalkerThreads = 128;  // threads per CTA of the thread-per-walker sweep
+constexpr long long kTuneMinWalkers = 512;  // below this, lane groups (a walker's chain sets the rate)
+
 // First-fit allocator over one device arena (offsets in bytes, 256-aligned).
 struct Arena {
     size_t size = 0;
@@ -118,11 +121,21 @@ struct rewl_server_s {
     int n_wins = 0;
     struct Cls {
         int bits = 4;
-        std::vector<rewl::SweepItem> items;
+        std::vector<rewl::SweepItem> items;      // lane groups: walker groups of one job
         rewl::SweepItem *d_items = nullptr;
         int threads = 0, grid = 0;
         size_t smem = 0;
+        std::vector<rewl::WalkerItem> walkers;   // a thread per walker: single walkers of any job
+        rewl::WalkerItem *d_walkers = nullptr;
+        int wgrid = 0;
     } cls[2];
+    // How the resident walkers map to threads: 32 (lane groups, state staged in
+    // shared memory) or 1 (a thread per walker, state in global memory).  Both
+    // compute the same states; when the resident walker count has changed by
+    // half since the last choice, the next two rounds time one mapping each and
+    // the faster is kept.
+    int lanes = 32;
+    long long tuned_walkers = 0;
     unsigned int *d_queues = nullptr;
     int sms = 0, optin = 0;
     // counters
@@ -149,6 +162,7 @@ rewl_status rebuild_tables(rewl_server_s *s) {
     std::vector<rewl::WinItem> wins;
     for (auto &c : s->cls) {
         c.items.clear();
+        c.walkers.clear();
         c.threads = 32;
         c.smem = 0;
     }
@@ -165,13 +179,16 @@ rewl_status rebuild_tables(rewl_server_s *s) {
         int P = (int)((size_t)s->optin / (size_t)d.lay.stride);
         P = std::max(1, std::min(P, 8));
         for (int g0 = 0; g0 < h->M.G; g0 += P) c.items.push_back({(int)i, g0, std::min(P, h->M.G - g0), 0});
+        for (int g = 0; g < h->M.G; ++g) c.walkers.push_back({(int)i, g});
         c.smem = std::max(c.smem, (size_t)P * (size_t)d.lay.stride);
         c.threads = std::max(c.threads, P * 32);
     }
     s->n_wins = (int)wins.size();
     const size_t need = align256(tab.size() * sizeof(rewl::InstDev) + 16) + align256(wins.size() * sizeof(rewl::WinItem) + 16) +
                         align256(s->cls[0].items.size() * sizeof(rewl::SweepItem) + 16) +
-                        align256(s->cls[1].items.size() * sizeof(rewl::SweepItem) + 16) + 256;
+                        align256(s->cls[1].items.size() * sizeof(rewl::SweepItem) + 16) +
+                        align256(s->cls[0].walkers.size() * sizeof(rewl::WalkerItem) + 16) +
+                        align256(s->cls[1].walkers.size() * sizeof(rewl::WalkerItem) + 16) + 256;
     if (need > s->tab_cap) {
         SRV_CUDA(cudaStreamSynchronize(s->stream));
         rewl::host::dev_free(s->tab_block);
@@ -188,6 +205,8 @@ rewl_status rebuild_tables(rewl_server_s *s) {
     for (auto &c : s->cls) {
         c.d_items = (rewl::SweepItem *)p;
         p += align256(c.items.size() * sizeof(rewl::SweepItem) + 16);
+        c.d_walkers = (rewl::WalkerItem *)p;
+        p += align256(c.walkers.size() * sizeof(rewl::WalkerItem) + 16);
     }
     s->d_queues = (unsigned int *)p;
     // the previous tables may still be read by queued rounds: order the copies
@@ -203,6 +222,9 @@ rewl_status rebuild_tables(rewl_server_s *s) {
         if (c.items.empty()) continue;
         SRV_CUDA(cudaMemcpyAsync(c.d_items, c.items.data(), c.items.size() * sizeof(rewl::SweepItem),
                                  cudaMemcpyHostToDevice, s->stream));
+        SRV_CUDA(cudaMemcpyAsync(c.d_walkers, c.walkers.data(), c.walkers.size() * sizeof(rewl::WalkerItem),
+                                 cudaMemcpyHostToDevice, s->stream));
+        c.wgrid = (int)((c.walkers.size() + kWalkerThreads - 1) / kWalkerThreads);
         SRV_CUDA(rewl::launch_batch_sweep(c.bits, 32, nullptr, nullptr, 0, nullptr, 0, c.threads, c.smem, nullptr, true));
         const int per_sm = std::max(1, rewl::batch_sweep_ctas_per_sm(c.bits, 32, c.threads, c.smem));
         c.grid = std::min((int)c.items.size(), per_sm * s->sms);
@@ -217,8 +239,12 @@ rewl_status enqueue_round(rewl_server_s *s) {
     for (int k = 0; k < 2; ++k) {
         auto &c = s->cls[k];
         if (c.items.empty()) continue;
-        SRV_CUDA(rewl::launch_batch_sweep(c.bits, 32, s->d_inst, c.d_items, (int)c.items.size(), s->d_queues + k,
-                                          c.grid, c.threads, c.smem, s->stream, false));
+        if (s->lanes == 1)
+            SRV_CUDA(rewl::launch_batch_walkers(c.bits, s->d_inst, c.d_walkers, (int)c.walkers.size(), c.wgrid,
+                                                kWalkerThreads, s->stream, false));
+        else
+            SRV_CUDA(rewl::launch_batch_sweep(c.bits, 32, s->d_inst, c.d_items, (int)c.items.size(), s->d_queues + k,
+                                              c.grid, c.threads, c.smem, s->stream, false));
     }
     SRV_CUDA(rewl::launch_batch_check(s->d_inst, s->d_wins, s->n_wins, s->stream));
     SRV_CUDA(rewl::launch_batch_exchange(s->d_inst, (int)s->running.size(), s->stream));
@@ -342,11 +368,39 @@ rewl_status rewl_server_step(rewl_server_t s, long long rounds, int *n_running, 
     rewl_status st = admit(s);
     if (st) return st;
     if (!s->running.empty()) {
+        long long left = rounds;
         if (s->tables_dirty) {
             st = rebuild_tables(s);
             if (st) return st;
+            long long walkers = 0;
+            for (long long id : s->running) walkers += s->jobs[id].inst->M.G;
+            if (walkers < kTuneMinWalkers) {
+                s->lanes = 32;
+                s->tuned_walkers = 0;
+            } else if (s->tuned_walkers == 0 || 2 * walkers > 3 * s->tuned_walkers ||
+                       3 * walkers < 2 * s->tuned_walkers) {
+                // one round in each mapping, timed on the stream; the faster stays
+                cudaEvent_t ev[3];
+                for (auto &e : ev) SRV_CUDA(cudaEventCreate(&e));
+                SRV_CUDA(cudaEventRecord(ev[0], s->stream));
+                s->lanes = 32;
+                st = enqueue_round(s);
+                if (st == REWL_OK) SRV_CUDA(cudaEventRecord(ev[1], s->stream));
+                s->lanes = 1;
+                if (st == REWL_OK) st = enqueue_round(s);
+                if (st == REWL_OK) SRV_CUDA(cudaEventRecord(ev[2], s->stream));
+                float t32 = 0.0f, t1 = 0.0f;
+                if (st == REWL_OK) SRV_CUDA(cudaEventSynchronize(ev[2]));
+                if (st == REWL_OK) SRV_CUDA(cudaEventElapsedTime(&t32, ev[0], ev[1]));
+                if (st == REWL_OK) SRV_CUDA(cudaEventElapsedTime(&t1, ev[1], ev[2]));
+                for (auto &e : ev) cudaEventDestroy(e);
+                if (st) return st;
+                s->lanes = t1 < t32 ? 1 : 32;
+                s->tuned_walkers = walkers;
+                left -= 2;
+            }
         }
-        for (long long r = 0; r < rounds && st == REWL_OK; ++r) st = enqueue_round(s);
+        for (long long r = 0; r < left && st == REWL_OK; ++r) st = enqueue_round(s);
         if (st) return st;
         // status of every running job, then retire the converged ones
         for (long long id : s->running) {
@@ -355,7 +409,7 @@ rewl_status rewl_server_step(rewl_server_t s, long long rounds, int *n_running, 
                                      s->stream));
         }
         SRV_CUDA(cudaStreamSynchronize(s->stream));
-        s->rounds_run += rounds;
+        s->rounds_run += (left < rounds ? 2 : 0) + std::max(0LL, left);
         std::vector<long long> keep;
         for (long long id : s->running) {
             Job &j = s->jobs[id];
@@ -386,6 +440,15 @@ rewl_status rewl_server_step(rewl_server_t s, long long rounds, int *n_running, 
     }
     if (n_running) *n_running = (int)s->running.size();
     if (n_queued) *n_queued = (int)s->queue.size();
+    return REWL_OK;
+    REWL_API_CATCH
+}
+
+rewl_status rewl_server_mapping(rewl_server_t s, int *lanes, long long *tuned_walkers) {
+    REWL_API_TRY
+    if (!s) return fail(REWL_ERR_ARG, "NULL server");
+    if (lanes) *lanes = s->lanes;
+    if (tuned_walkers) *tuned_walkers = s->tuned_walkers;
     return REWL_OK;
     REWL_API_CATCH
 }

@@ -343,6 +343,12 @@ class Server:
         return {"t_submit": t[0], "t_admit": t[1], "t_done": t[2], "rounds": int(c[0]), "flips": int(c[1]),
                 "bytes": int(c[2])}
 
+    def mapping(self):
+        """(lanes, resident walkers when it was chosen): 32 lane groups or 1 thread per walker."""
+        ln, w = C.c_int(0), C.c_longlong(0)
+        check(self._L.rewl_server_mapping(self._h, C.byref(ln), C.byref(w)))
+        return ln.value, w.value
+
     def cancel(self, job):
         check(self._L.rewl_server_cancel(self._h, job))
 

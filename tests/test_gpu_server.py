@@ -115,3 +115,25 @@ def test_release_forgets_finished_jobs():
     other = srv.submit(**j)
     srv.cancel(other)
     srv.release(other)
+
+
+def test_many_resident_walkers_switch_mapping_without_changing_results():
+    """From 512 resident walkers on the server times lane groups against a
+    thread per walker whenever the resident set changes by half, and keeps the
+    faster; the jobs' results stay exactly their alone results and the states
+    after a fixed number of rounds those of the same rounds alone."""
+    jobs = [dict(q=10, L=12, h=16, overlap=0.75, m=8, lnf_final=1e-3, flatness=0.8, exchange_interval=500, seed=s)
+            for s in range(1, 5)]  # 4 x 128 walkers
+    srv = Server(pool_bytes=512 << 20, max_jobs=8)
+    ids = [srv.submit(**j) for j in jobs]
+    srv.step(rounds=3)
+    lanes, tuned = srv.mapping()
+    assert tuned == 512 and lanes in (1, 32)
+    ticks = 0
+    while srv.info()["running"]:
+        srv.step(rounds=4)
+        ticks += 1
+        assert ticks < 100000
+    for i, j in zip(ids, jobs):
+        assert srv.poll(i) == "done"
+        assert same(srv.result(i), alone_result(j))
