@@ -72,6 +72,8 @@ def parse_args():
                          "two, so every WL step takes the binary64 add)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--jobs", type=int, default=100, help="arrivals of the serving trace")
+    ap.add_argument("--instances", type=int, default=2048,
+                    help="batched2048: instances of the batch (fewer only for small profiler captures)")
     ap.add_argument("--cost-cap", type=float, default=1e10,
                     help="serving_full: jobs whose estimated cost exceeds this many proposals are left out")
     ap.add_argument("--converge", default="",
@@ -530,7 +532,7 @@ def run_batched(args):
     from paper_1312_3004_gb300 import REWL, Batch
     from paper_1312_3004_gb300 import workloads as WL
 
-    jobs = WL.batched_instances(2048)
+    jobs = WL.batched_instances(args.instances)
     stream = torch.cuda.Stream()
 
     # the batched form: created with the size rule, then the autotuner times its
@@ -593,7 +595,8 @@ def run_batched(args):
     line = {"metric": "flip attempts/s", "value": value, "unit": "flips/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "batched2048", "instances": info["instances"], "walkers": info["walkers"],
+            "config": {"workload": "batched2048" if args.instances == 2048 else "batched%d" % args.instances,
+                       "instances": info["instances"], "walkers": info["walkers"],
                        "device_bytes": info["device_bytes"], "create_s": t_create,
                        "l2": "state larger than L2 (%.0f MB)" % (info["device_bytes"] / 1e6)},
             "plain": {"value": plain, "unit": "flips/s", "instances_sampled": len(sample),
