@@ -53,7 +53,7 @@ LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 # DRAM bytes (read + write) of one sweep launch, from ncu captures of the
 # current kernels (profiles/sweep_fast_potts10_L80.md, profiles/batch_walker_batched2048.md)
-TRAFFIC_PER_LAUNCH = {"potts10_L80": 10.12e6, "batched2048": 6.40e9}
+TRAFFIC_PER_LAUNCH = {"potts10_L80": 10.12e6, "batched2048": 6.16e9}
 
 
 def parse_args():
@@ -591,7 +591,7 @@ def run_batched(args):
     f_hz = (clocks.get("sm_mhz") or pipes["max_clock_mhz"]) * 1e6
     bounds = pipe_bounds(pipes, f_hz, 0.0)  # no exp charged: the oracle is not run here
     binding = min(bounds, key=bounds.get)
-    captured = cfg == {"spin_bits": 8, "lanes": 1, "cta_kb": 0, "threads": 256}
+    captured = args.instances == 2048 and cfg == {"spin_bits": 8, "lanes": 1, "cta_kb": 0, "threads": 128}
     line = {"metric": "flip attempts/s", "value": value, "unit": "flips/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
