@@ -72,6 +72,8 @@ def parse_args():
                          "two, so every WL step takes the binary64 add)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--jobs", type=int, default=100, help="arrivals of the serving trace")
+    ap.add_argument("--autotune", action="store_true",
+                    help="single-instance workloads: time every lane width first (rewl_autotune) and keep the fastest")
     ap.add_argument("--instances", type=int, default=2048,
                     help="batched2048: instances of the batch (fewer only for small profiler captures)")
     ap.add_argument("--cost-cap", type=float, default=1e10,
@@ -374,6 +376,8 @@ def run_ours(args):
         r.run_phase(_lib.PHASE_EXCHANGE)
         e2.record(stream)
 
+    tuned = r.autotune(2) if args.autotune else None  # ordinary rounds; the fastest lane width stays
+    pre_rounds = r.round
     for _ in range(args.warmup):
         with torch.cuda.stream(stream):
             flush.zero_()
@@ -420,6 +424,9 @@ def run_ours(args):
     if args.schedule == "inv_t":
         r2.set_option(_lib.OPT_SCHEDULE, _lib.SCHEDULE_INV_T)
         r2.set("phase", 1)
+    if pre_rounds:  # the rounds the autotuner ran on the first handle, in the chosen lane width
+        r2.set_option(_lib.OPT_LANES, r.get_option(_lib.OPT_LANES))
+        r2.run(pre_rounds)
     for _ in range(args.warmup):
         with torch.cuda.stream(stream):
             flush.zero_()
@@ -507,6 +514,7 @@ def run_ours(args):
                        "walkers_per_cta": r.get_option(_lib.OPT_WALKERS_PER_CTA),
                        "lattice": "global" if r.get_option(_lib.OPT_LATTICE) else "shared"},
         "slow_path_decisions": r.stats()["slow_decisions"],
+        "autotune": {"timed": tuned, "rounds_before_warmup": pre_rounds} if tuned is not None else None,
         "clocks": clocks,
         "wall_s_timed": wall,
         "sweep_share": sum(sweep_ms) / total_ms,
