@@ -622,7 +622,10 @@ SweepPlan plan_sweep(const Model &M, int num_sms, size_t smem_optin, int kind, i
         // the rate); a thread per walker, state in global memory, once there are
         // enough of them to fill the SMs by themselves (measured crossover on
         // GB300: between 4096 and 16384 walkers)
-        if (lanes <= 0) lanes = M.G <= 80 * num_sms ? 32 : 1;
+        // (tiny lattices: 32 proposals of a batch touch each other's neighbourhoods
+        // so often that 8-lane trees win -- measured on the L = 8 Ising workload:
+        // 2.13e7 flips/s with 8 lanes against 1.74e7 with 32)
+        if (lanes <= 0) lanes = M.G <= 80 * num_sms ? (M.N <= 128 ? 8 : 32) : 1;
         p.lanes = lanes;
         p.lat_global = lat_mode == 1   ? 1
                        : lat_mode == 2 ? 0
