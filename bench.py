@@ -72,6 +72,8 @@ def parse_args():
                          "two, so every WL step takes the binary64 add)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--jobs", type=int, default=100, help="arrivals of the serving trace")
+    ap.add_argument("--production", action="store_true",
+                    help="time fixed-weight production rounds (H(E,O)) on the workload after --warmup WL rounds")
     ap.add_argument("--autotune", action="store_true",
                     help="single-instance workloads: time every lane width first (rewl_autotune) and keep the fastest")
     ap.add_argument("--instances", type=int, default=2048,
@@ -784,6 +786,38 @@ def run_serving_full(args):
     print(json.dumps(line), flush=True)
 
 
+def run_production(args):
+    """Fixed-weight production (Sec. 3.2) on a named workload: --warmup WL
+    rounds first (the walkers' ln g is then their estimate so far), then
+    production with H(E, O) of the majority count in 64 classes; --steps
+    production rounds are timed with events on the handle's stream."""
+    import torch
+
+    from paper_1312_3004_gb300 import REWL
+    from paper_1312_3004_gb300 import workloads as WL
+
+    p = WL.params(args.workload)
+    stream = torch.cuda.Stream()
+    r = REWL(*WL.rewl_args(p, args.seed), spin_bits=p["spin_bits"], stream=stream)
+    r.run(max(1, args.warmup))
+    r.production_start(64)
+    r.production_run(1)
+    f0 = r.stats()["flips"]
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    r.production_run(args.steps)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    flips = r.stats()["flips"] - f0
+    print(json.dumps({"metric": "production flip attempts/s", "value": flips / (ms / 1e3), "unit": "flips/s",
+                      "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                      "higher_is_better": True, "data": "synthetic", "gpu_launches": 2 * args.steps,
+                      "config": dict(config_of(args.workload, p), production_classes=64),
+                      "heo_total": int(r.heo().sum())}), flush=True)
+
+
 def analyse(r, p):
     """Canonical analysis of a converged run's joined ln g through the
     library: the specific-heat maximum and the equal-peak temperature Tc(L)
@@ -961,6 +995,8 @@ def main():
     args = parse_args()
     if args.converge:
         run_converge(args)
+    elif args.production:
+        run_production(args)
     elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched2048":
