@@ -248,7 +248,8 @@ __global__ void __launch_bounds__(256) sweep_kernel(Model M, State S, int P) {
 // sampled with the fixed weights 1/g(E) and distributions H(E, O) recorded).
 // Each walker keeps its own final ln g and ln f = 0, so a WL step is a
 // Metropolis step inside the window with the same decision as the sweep
-// (accept iff D >= 0 or u < exp(D)); after every step the window's H(E, O)
+// (accept iff D >= 0 or u < exp(D), exp evaluated only when a single-precision
+// bracket of -ln u cannot decide); after every step the window's H(E, O)
 // counts the current energy and the class of the majority count
 // O = max_v #{i : s_i = v} of the configuration, one of n_obins equal integer
 // classes of [ceil(N/q), N].  Every window runs, finished or not; H stays 0.
@@ -256,9 +257,11 @@ __global__ void __launch_bounds__(256) sweep_kernel(Model M, State S, int P) {
 // configuration buffer in global memory (the thread owns that buffer for the
 // launch); runs of equal (E, O) are added to H(E, O) with one atomic each.
 template <int BITS>
-__global__ void __launch_bounds__(128) production_kernel(Model M, State S) {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= M.G) return;
+__global__ void __launch_bounds__(256) production_kernel(Model M, State S, int per) {
+    // per walkers per CTA (the CTA is a whole number of warps, the rest idle):
+    // spread over every SM, since each walker's chain, not a pipe, sets its rate
+    const int g = blockIdx.x * per + (int)threadIdx.x;
+    if ((int)threadIdx.x >= per || g >= M.G) return;
     const int w = g / M.m;
     const int lo = S.e_lo[w], hi = lo + M.W;
     const uint32_t c = S.slot_cfg[g];
@@ -287,10 +290,35 @@ __global__ void __launch_bounds__(128) production_kernel(Model M, State S) {
             const double d = __dsub_rn(lg[REWL_IDX(E - lo, 0, M.B, bad)], lg[REWL_IDX(En - lo, 0, M.B, bad)]);
             bool acc = d >= 0.0;
             if (!acc) {
-                const double u = unit53(r.z, r.w);
-                const double e = exp(d);
-                acc = u < e;
-                if (fabs(u - e) < 1e-14) record_tie(S.ctl, S.tlog, TIE_WL, (unsigned int)g, t);
+                // The reference decision u < exp(d), taken first against a
+                // bracket of -ln u from single precision: uf is u to 2^-23
+                // relative (the 24 + 24 bits below carry one rounding, and the
+                // dropped 5 bits are under 2^-24 of u once the top 24 bits are
+                // not all zero), logf is within one ulp, so |Lf + ln u| is below
+                // (Lf + 1) 2^-22.9; the margin (Lf + 1) 2^-18 leaves a factor
+                // over 20 for that and for exp's own rounding (one ulp of a
+                // double).  Outside the bracket the binary64 comparison can only
+                // come out as the bracket says; inside it (about 1e-5 of the
+                // decisions) exp(d) decides, as in the reference.
+                const unsigned long long U = ((unsigned long long)(r.z >> 5) << 26) | (r.w >> 6);
+                const uint32_t top = (uint32_t)(U >> 29);
+                int sure = 0;  // 1: accept, -1: reject, 0: take the exact path
+                if (top != 0u) {
+                    const float uf = fmaf((float)top, 0x1p-24f, (float)((uint32_t)(U >> 5) & 0xffffffu) * 0x1p-48f);
+                    const float Lf = -logf(uf);
+                    const float margin = (Lf + 1.0f) * 0x1p-18f;
+                    const double nd = -d;
+                    if (nd < (double)(Lf - margin)) sure = 1;
+                    else if (nd >= (double)(Lf + margin)) sure = -1;
+                }
+                if (sure != 0) {
+                    acc = sure > 0;
+                } else {
+                    const double u = unit53(r.z, r.w);
+                    const double e = exp(d);
+                    acc = u < e;
+                    if (fabs(u - e) < 1e-14) record_tie(S.ctl, S.tlog, TIE_WL, (unsigned int)g, t);
+                }
             }
             if (acc) {
                 spin_set<BITS>(lat, site, nw);
@@ -699,9 +727,15 @@ cudaError_t launch_count_spins(const Model &M, const State &S, cudaStream_t s) {
 }
 
 cudaError_t launch_production_sweep(const Model &M, const State &S, cudaStream_t s) {
-    const int threads = 128, grid = (M.G + threads - 1) / threads;
-    if (M.bits == 8) production_kernel<8><<<grid, threads, 0, s>>>(M, S);
-    else production_kernel<4><<<grid, threads, 0, s>>>(M, S);
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    int per = (M.G + sms - 1) / sms;  // walkers per CTA: one CTA per SM
+    if (per > 256) per = 256;
+    const int threads = ((per + 31) / 32) * 32, grid = (M.G + per - 1) / per;
+    if (M.bits == 8) production_kernel<8><<<grid, threads, 0, s>>>(M, S, per);
+    else production_kernel<4><<<grid, threads, 0, s>>>(M, S, per);
     return cudaGetLastError();
 }
 

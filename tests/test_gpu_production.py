@@ -67,3 +67,38 @@ def test_production_restart_and_refusals():
     assert gpu.heo().sum() == 0
     gpu.production_run(1)
     assert int(gpu.heo().sum()) == 400 * gpu.G
+
+
+def test_a_planted_near_tie_in_production_is_logged():
+    """ln g set so that the first production step of one walker has exp(D)
+    within 1e-16 of its draw: the production kernel's single-precision bracket
+    cannot decide it, the exact binary64 path does and logs the near tie, and
+    the oracle sees the same near tie; the states agree or differ by that one
+    decision."""
+    from tie_trace import gpu_ties, planted_near_tie
+
+    args = (3, 5, 2, 0.75, 2, 1e-3, 0.8, 200, 11)
+    for g in range(4):
+        if planted_near_tie(O.OracleREWL(*args), 11, g):
+            break
+    else:
+        pytest.skip("no walker's first proposal stays in its window")
+    gpu, orc = REWL(*args), O.OracleREWL(*args)
+    gpu.production_start(4)
+    orc.production_start(4)
+    planted_near_tie(orc, 11, g, setter=lambda lng: gpu.set("lng", lng))
+    gpu.production_run(1)
+    orc.production_run(1)
+    n, log = gpu_ties(gpu)
+    assert n >= 1 and (0, g, 0) in log
+    _, seen = orc.ties()
+    assert any(e[:3] == (0, g, 0) and e[3] < 1e-14 for e in seen)
+    if differing(gpu_state(gpu), oracle_state(orc)):  # the two exps decided differently
+        o2 = O.OracleREWL(*args)
+        o2.production_start(4)
+        planted_near_tie(o2, 11, g)
+        o2.invert_decision(0, g, 0)
+        o2.production_run(1)
+        assert not differing(gpu_state(gpu), oracle_state(o2)) and np.array_equal(gpu.heo(), o2.heo())
+    else:
+        assert np.array_equal(gpu.heo(), orc.heo())
