@@ -72,6 +72,8 @@ def parse_args():
                          "two, so every WL step takes the binary64 add)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--jobs", type=int, default=100, help="arrivals of the serving trace")
+    ap.add_argument("--weak-scaling", default="",
+                    help="comma-separated workloads run together to convergence (one seed, --converge-limit)")
     ap.add_argument("--production", action="store_true",
                     help="time fixed-weight production rounds (H(E,O)) on the workload after --warmup WL rounds")
     ap.add_argument("--autotune", action="store_true",
@@ -818,6 +820,62 @@ def run_production(args):
                       "heo_total": int(r.heo().sum())}), flush=True)
 
 
+def run_weak_scaling(args):
+    """Time to convergence of several workloads run together, one stream
+    each, one seed (the GPU analogue of Fig. 4's weak scaling: as N grows
+    the number of windows grows, each window keeps its width, and the paper
+    finds the time to a full density of states almost constant)."""
+    import torch
+
+    from paper_1312_3004_gb300 import REWL
+    from paper_1312_3004_gb300 import workloads as WL
+
+    names = [x for x in args.weak_scaling.split(",") if x]
+    props = torch.cuda.get_device_properties(0)
+    uuid = getattr(props, "uuid", None)
+    uuid = ("GPU-" + str(uuid)) if uuid is not None and not str(uuid).startswith("GPU-") else uuid
+    sampler = ClockSampler(uuid if uuid else None)
+    sampler.start()
+    epoch0 = time.time()
+    hs = []
+    for n in names:
+        p = WL.params(n)
+        hs.append((n, p, REWL(*WL.rewl_args(p, args.seed), spin_bits=p["spin_bits"], stream=torch.cuda.Stream())))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    finish, traces, el, last = {}, {n: [] for n in names}, 0.0, 0.0
+    while len(finish) < len(hs) and el < args.converge_limit:
+        for n, _, r in hs:
+            if n not in finish:
+                r.run_async(50)
+        for n, _, r in hs:
+            if n not in finish and r.sync():
+                finish[n] = time.perf_counter() - t0
+                print(json.dumps({"converged": n, "seconds": finish[n]}), flush=True)
+        el = time.perf_counter() - t0
+        if el - last >= 60.0:
+            last = el
+            for n, _, r in hs:
+                st = r.stats()
+                traces[n].append([round(el, 1), st["windows_done"], st["max_lnf"]])
+            print(json.dumps({"progress_s": round(el, 1), "runs": {k: v[-1][1:] for k, v in traces.items() if v}}),
+                  flush=True)
+    clocks = sampler.stop(epoch0, time.time())
+    runs = []
+    for n, p, r in hs:
+        st = r.stats()
+        secs = finish.get(n, el)
+        runs.append({"workload": n, "N": p["L"] ** 2, "windows": p["h"], "bins_per_window": r.W + 1,
+                     "walkers": p["h"] * p["m"], "converged": n in finish, "seconds": secs, "rounds": st["rounds"],
+                     "flips": st["flips"], "steps_per_walker": st["flips"] / (p["h"] * p["m"]),
+                     "windows_done": st["windows_done"], "progress": traces[n],
+                     "analysis": analyse(r, p) if n in finish else None})
+        r.close()
+    print(json.dumps({"metric": "time to converge, weak scaling", "unit": "s", "higher_is_better": False,
+                      "n_gpus": 1, "data": "synthetic", "seed": args.seed, "limit_s": args.converge_limit,
+                      "clocks": clocks, "runs": runs}), flush=True)
+
+
 def analyse(r, p):
     """Canonical analysis of a converged run's joined ln g through the
     library: the specific-heat maximum and the equal-peak temperature Tc(L)
@@ -997,6 +1055,8 @@ def main():
         run_converge(args)
     elif args.production:
         run_production(args)
+    elif args.weak_scaling:
+        run_weak_scaling(args)
     elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched2048":

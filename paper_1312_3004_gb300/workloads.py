@@ -30,6 +30,13 @@ CONFIGS = {
     # 1000 bins at 75% overlap, 3 walkers each (2151 walkers), 4-bit spins (45 KB lattices)
     "potts10_L300": dict(q=10, L=300, h=717, overlap=0.75, m=3, lnf_final=1e-8, flatness=0.8,
                          exchange_interval=10_000, spin_bits=4),
+    # Weak scaling (Sec. 3.1, Fig. 4: the number of windows grows with N so that each
+    # window keeps its width): 10-state Potts at L = 40 and 80 with windows of 291 + 1
+    # bins, as the L=20 workload's, 4 walkers each
+    "potts10_L40_w291": dict(q=10, L=40, h=41, overlap=0.75, m=4, lnf_final=1e-8, flatness=0.8,
+                             exchange_interval=10_000, spin_bits=8),
+    "potts10_L80_w291": dict(q=10, L=80, h=173, overlap=0.75, m=4, lnf_final=1e-8, flatness=0.8,
+                             exchange_interval=10_000, spin_bits=4),
 }
 
 
