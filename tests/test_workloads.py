@@ -70,3 +70,14 @@ def test_job_cost_estimate_reproduces_its_calibration_runs():
         measured = statistics.median(r["wl_steps"] for r in runs)
         est = WL.job_cost_estimate(WL.params("potts10_L%d" % L))
         assert 1 / 1.3 < est / measured < 1.3, (L, est, measured)
+
+
+def test_weak_scaling_workloads_keep_the_window_width():
+    """Sec. 3.1 / Fig. 4: the windows grow in number with N and keep their width;
+    at L = 20, 40 and 80 the window formula gives 291 + 1 bins each."""
+    from oracle import oracle as O
+
+    for name in ("potts10_L20", "potts10_L40_w291", "potts10_L80_w291"):
+        p = WL.params(name)
+        assert O.window_table(p["L"], p["h"], p["overlap"])[1] == 291, name
+        assert p["m"] == 4 and p["lnf_final"] == 1e-8
