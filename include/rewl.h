@@ -151,7 +151,8 @@ rewl_status rewl_run_phase(rewl_t h, int phase);
  *   REWL_OPT_LANES         lanes per walker of the fast sweep: 0 = chosen from
  *                          the walker count and lattice size (up to 80 walkers
  *                          per SM 32, or 8 for lattices of at most 128 sites;
- *                          else 1), or
+ *                          else 1; and 1 whenever a lane group's ln g shadow
+ *                          would not fit in shared memory), or
  *                          1, 2, 4, 8, 16, 32
  *   REWL_OPT_WALKERS_PER_CTA  (read-only) walkers per CTA of the current plan
  *   REWL_OPT_LATTICE       where the fast sweep keeps the lattices: set 0 =

@@ -653,7 +653,13 @@ SweepPlan plan_sweep(const Model &M, int num_sms, size_t smem_optin, int kind, i
         // (tiny lattices: 32 proposals of a batch touch each other's neighbourhoods
         // so often that 8-lane trees win -- measured on the L = 8 Ising workload:
         // 2.13e7 flips/s with 8 lanes against 1.74e7 with 32)
-        if (lanes <= 0) lanes = M.G <= 80 * num_sms ? (M.N <= 128 ? 8 : 32) : 1;
+        const bool chosen = lanes <= 0;
+        if (chosen) lanes = M.G <= 80 * num_sms ? (M.N <= 128 ? 8 : 32) : 1;
+        // a window too wide for a lane group's shared memory (its ln g shadow):
+        // a thread per walker with the whole state in global memory
+        if (chosen && lanes > 1 && lat_mode != 2 &&
+            fast_smem_per_walker(M, lanes, M.wpc * 4 > kSharedLatticeMax) > smem_optin)
+            lanes = 1;
         p.lanes = lanes;
         p.lat_global = lat_mode == 1   ? 1
                        : lat_mode == 2 ? 0

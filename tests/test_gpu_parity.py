@@ -391,3 +391,22 @@ def test_autotune_changes_no_result(case):
     gpu.run(3)
     orc.run(gpu.round)
     assert_parity(gpu, orc)
+
+
+@pytest.mark.parametrize("case", [
+    (10, 1024, 2, 0.75, 1, 1e-6, 0.8, 500, 4, 8),     # the largest L: 2^20 sites, windows of 1.7e6 bins
+    (200, 12, 3, 0.75, 2, 1e-3, 0.8, 2000, 5, 8),     # q far above 16: 8-bit spins only
+    (2, 3, 1, 0.0, 1, 1e-3, 0.8, 1, 6, 8),            # the smallest lattice, no overlap, K = 1
+])
+def test_extreme_sizes_match(case):
+    """Sizes at the edges of the interface: L = 1024 (the lane group's ln g
+    shadow cannot fit in shared memory, so the plan falls back to a thread
+    per walker with its state in global memory), q = 200, and L = 3 with one
+    window, one walker and an exchange round after every step."""
+    from paper_1312_3004_gb300 import _lib
+    *args, sb = case
+    tp = traced(*args, spin_bits=sb)
+    if args[1] == 1024:
+        assert tp.test.get_option(_lib.OPT_LANES) == 1 and tp.test.get_option(_lib.OPT_LATTICE) == 1
+    for n in (1, 2):
+        tp.run(n)
