@@ -113,3 +113,36 @@ def test_converge_report_compares_with_the_oracle_values():
     assert bench.oracle_reference("potts10_L8", r1["seed"], moved, None)["same_as_oracle"] is False
     assert bench.oracle_reference("potts10_L8", 99, same, None).get("oracle_same_seed") is None
     assert bench.oracle_reference("no_such_workload", 1, same, None) is None
+
+
+def test_pipe_bounds_take_the_smallest_pipe():
+    """The per-flip roofline: each pipe's rate x SMs x clock / its operations
+    per flip; with GB300's measured rates the FP64 pipe binds once exp is
+    charged for the decisions with D < 0, and the issue bound equals
+    152 x 128 lanes x f / 103."""
+    import bench
+
+    pipes = {"sms": 152, "dadd": 1.68, "imad": 64.2, "imad_hi": 32.0, "lop3": 64.2, "iadd": 128.6, "lds": 23.0}
+    f = 2.07e9
+    b = bench.pipe_bounds(pipes, f, 0.62)
+    assert min(b, key=b.get) == "fp64"
+    assert abs(b["issue"] - 152 * 128 * f / 103) < 1e-3 * b["issue"]
+    assert abs(b["fp64"] - 152 * 1.68 * f / (2 + 20 * 0.62)) < 1e-6 * b["fp64"]
+    assert bench.pipe_bounds(pipes, f, 0.0)["fp64"] > b["fp64"]  # no exp charged: a higher bound
+
+
+def test_bench_modes_parse():
+    import sys
+
+    import bench
+
+    argv = sys.argv
+    try:
+        sys.argv = ["bench.py", "--weak-scaling", "potts10_L20,potts10_L40_w291", "--converge-limit", "60"]
+        a = bench.parse_args()
+        assert a.weak_scaling.split(",") == ["potts10_L20", "potts10_L40_w291"] and a.converge_limit == 60
+        sys.argv = ["bench.py", "--production", "--autotune", "--instances", "512", "--converge-save", "d"]
+        a = bench.parse_args()
+        assert a.production and a.autotune and a.instances == 512 and a.converge_save == "d"
+    finally:
+        sys.argv = argv
