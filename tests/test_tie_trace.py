@@ -114,3 +114,20 @@ def test_the_oracle_logs_a_planted_near_tie():
     assert n >= 1
     hit = [e for e in log if e[:3] == (0, g, 0)]
     assert hit and hit[0][3] < 1e-14
+
+
+def test_decision_counts_of_flat_weights():
+    """The counts behind the roofline's exp fraction: with ln g flat and
+    ln f = 0 every decision inside the window has D = 0 (none needs exp, every
+    one accepts); in an ordinary run some have D < 0, and no count exceeds the
+    steps made."""
+    o = O.OracleREWL(*ARGS)
+    o.production_start(4)  # ln f = 0; ln g is still all zero
+    o.production_run(2)
+    n, neg = o.decision_counts()
+    assert n > 0 and neg == 0
+    assert n <= int(o.t().sum())
+    r = O.OracleREWL(*ARGS)
+    r.run(3)
+    n2, neg2 = r.decision_counts()
+    assert 0 < neg2 < n2 <= int(r.t().sum())
